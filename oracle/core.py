@@ -1,0 +1,121 @@
+"""ctypes binding of the C oracle (lcdm_oracle.c).  Test infrastructure only."""
+import ctypes
+import numpy as np
+
+from . import build as _build
+
+OUT_NAMES = ("d_C", "t", "X", "d_M", "d_L", "mu")
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        lib.oracle_quad_distances.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp,
+                                              ctypes.c_int64, ctypes.c_double, dp, dp]
+        lib.oracle_carlson_distances.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp,
+                                                 ctypes.c_int64, dp, i32p, i32p, dp, dp]
+        lib.oracle_carlson_batch.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp]
+        lib.oracle_simpson.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp]
+        lib.oracle_set_mutation.argtypes = [ctypes.c_int]
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def set_mutation(m: int) -> None:
+    """Plant a deliberate mistake (tests only); 0 restores the correct oracle."""
+    _load().oracle_set_mutation(int(m))
+
+
+_KIND = {"rf": 0, "rj": 1, "rc": 2, "rd": 3}
+
+
+def carlson(kind: str, *args) -> np.ndarray:
+    """Vectorised Carlson integral R_F / R_J / R_C / R_D (eqs. 2.6-2.9).
+
+    Arguments broadcast; complex allowed.  Returns complex128.
+    """
+    arrs = np.broadcast_arrays(*[np.asarray(a, dtype=np.complex128) for a in args])
+    shape = arrs[0].shape
+    n = int(np.prod(shape)) if shape else 1
+    packed = np.zeros((n, 8))
+    for k, a in enumerate(arrs):
+        a = a.reshape(-1)
+        packed[:, 2 * k] = a.real
+        packed[:, 2 * k + 1] = a.imag
+    out = np.zeros((n, 2))
+    _load().oracle_carlson_batch(_KIND[kind], n, _dp(packed), _dp(out))
+    return (out[:, 0] + 1j * out[:, 1]).reshape(shape)
+
+
+def _csr(params, z, offsets):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    if params.ndim == 1:
+        params = params[None, :]
+    z = np.ascontiguousarray(z, dtype=np.float64).reshape(-1)
+    B, ncol = params.shape
+    if offsets is None:
+        if z.size % B:
+            raise ValueError("dense layout needs nnz divisible by B")
+        offsets = np.arange(B + 1, dtype=np.int64) * (z.size // B)
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    return params, z, offsets, B, ncol
+
+
+def quad_distances(params, z, offsets=None, rtol=1e-14, grad=False):
+    """O1 (+ O4): quadrature of (2.3)-(2.5).  Returns out[nnz, 6] (OUT_NAMES)
+    and, when grad, jac[nnz, 6, ncol] (derivatives w.r.t. the param columns)."""
+    params, z, offsets, B, ncol = _csr(params, z, offsets)
+    out = np.zeros((z.size, 6))
+    jac = np.zeros((z.size, 6, ncol)) if grad else None
+    _load().oracle_quad_distances(
+        _dp(params), B, ncol, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        _dp(z), z.size, rtol, _dp(out), _dp(jac) if grad else None)
+    return (out, jac) if grad else out
+
+
+def carlson_distances(params, z, offsets=None, roots=None, perm=None, return_imag=False):
+    """O2: eqs. (3.7)-(3.9) / (B.1)-(B.3) from roots of E^2 in x = 1+z.
+
+    roots/perm default to ``roots.roots_x`` / ``roots.permutations``.
+    """
+    from . import roots as _roots
+    params, z, offsets, B, ncol = _csr(params, z, offsets)
+    if roots is None:
+        rho, nroot = _roots.roots_x(params)
+    else:
+        rho, nroot = roots
+    if perm is None:
+        perm = _roots.permutations(rho, nroot)
+    packed = np.zeros((B, 4, 2))
+    packed[:, :, 0] = rho.real
+    packed[:, :, 1] = rho.imag
+    packed = np.ascontiguousarray(packed)
+    nroot = np.ascontiguousarray(nroot, dtype=np.int32)
+    perm = np.ascontiguousarray(perm, dtype=np.int32)
+    out = np.zeros((z.size, 6))
+    imag = np.zeros((z.size, 3))
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _load().oracle_carlson_distances(
+        _dp(params), B, ncol, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        _dp(z), z.size, _dp(packed), nroot.ctypes.data_as(i32p), perm.ctypes.data_as(i32p),
+        _dp(out), _dp(imag))
+    return (out, imag) if return_imag else out
+
+
+def simpson(param_row, z, n=1_000_000):
+    """Brute-force composite Simpson rule of (2.3)-(2.5) on n subintervals."""
+    p = np.ascontiguousarray(param_row, dtype=np.float64)
+    res = np.zeros(3)
+    _load().oracle_simpson(_dp(p), p.size, float(z), int(n), _dp(res))
+    return res

@@ -1,0 +1,602 @@
+/*
+ * lcdm_oracle.c -- plain FP64 CPU oracle for LambdaCDM+radiation+curvature
+ * distances (Karchev, "Analytic auto-differentiable LambdaCDM cosmography").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline / reference legs of bench.py may load this library.  It shares
+ * no code, header, table or constant with the CUDA path and never calls it.
+ *
+ * Contents (each function cites the passage it follows):
+ *   O1  oracle_quad_distances : adaptive Gauss-Legendre quadrature of the
+ *       defining integrals (2.3)-(2.5), written in the scale factor a.
+ *   O4  (same call, jac != NULL): Leibniz-rule gradients of the same
+ *       integrals with respect to the density parameters (fn23 of the paper
+ *       describes this approach), plus the curvature / modulus chain rule.
+ *   O2  oracle_carlson_distances : eqs. (3.7)-(3.9) (quartic) and
+ *       (B.1)-(B.3) (cubic) assembled in complex FP64 from given roots.
+ *   Carlson R_F, R_J, R_C, R_D (eqs. 2.6-2.9) by Carlson's duplication
+ *       algorithm (the paper's ref. [10]), complex arguments, with Cauchy
+ *       principal values for negative real w (R_J) and y (R_C) (Sec. 2.2).
+ *
+ * Everything is written for clarity, not speed: no blocking, no fusion.
+ */
+#include <complex.h>
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef double complex cplx;
+
+/* Physical constants (standard values, stated here independently). */
+#define C_KMS 299792.458                 /* speed of light, km/s            */
+#define HUBBLE_TIME_GYR 977.7922216807891 /* (1 Mpc / 1 km) / (1 Gyr / 1 s)  */
+/* 1 Mpc = 3.0856775814913673e19 km; 1 Gyr = 1e9 Julian years of 365.25 d.  */
+
+/* ------------------------------------------------------------------------ */
+/* Deliberate-mistake switch.  Tests set a non-zero value to check that the  */
+/* pins catch a plausible error; 0 (default) is the correct oracle.          */
+/*   1: drop the E3/14 term of the R_F series                                */
+/*   2: flip the sign of the R_C term in eq. (3.8)                           */
+/*   3: transpose X_i <-> Y_i in u_ij (quartic and cubic)                    */
+/*   4: drop the (1+z) factor of the luminosity distance                     */
+/*   5: drop the -a^2 closure term from the Omega_m Leibniz gradient          */
+/*   6: replace R_C(1, 1+e_m) by 1 in the duplication sum of R_J            */
+/* ------------------------------------------------------------------------ */
+static int g_mutation = 0;
+void oracle_set_mutation(int m) { g_mutation = m; }
+
+/* ======================================================================== */
+/* Carlson symmetric integrals by duplication (ref. [10]).                  */
+/* Tolerance r: the series is truncated once every normalised deviation is  */
+/* below the level at which the neglected terms are smaller than r.         */
+/* ======================================================================== */
+#define CARLSON_R 1e-17
+#define CARLSON_MAXIT 200
+
+static double maxabs3(cplx a, cplx b, cplx c) {
+    double m = cabs(a);
+    if (cabs(b) > m) m = cabs(b);
+    if (cabs(c) > m) m = cabs(c);
+    return m;
+}
+
+/* R_C(x, y) = R_F(x, y, y), eq. (2.8). */
+static cplx rc_dup(cplx x, cplx y) {
+    cplx A0 = (x + 2.0 * y) / 3.0, A = A0;
+    double Q = pow(3.0 * CARLSON_R, -1.0 / 8.0) * cabs(A0 - x);
+    double f = 1.0; /* 4^-m */
+    int m = 0;
+    while (f * Q >= cabs(A) && m < CARLSON_MAXIT) {
+        cplx lam = 2.0 * csqrt(x) * csqrt(y) + y;
+        A = (A + lam) / 4.0; x = (x + lam) / 4.0; y = (y + lam) / 4.0;
+        f /= 4.0; m++;
+    }
+    cplx s = (y - A) / A; /* deviation of y from the running mean */
+    cplx series = 1.0 + s * s * (3.0 / 10.0 + s * (1.0 / 7.0 + s * (3.0 / 8.0 + s * (9.0 / 22.0
+                  + s * (159.0 / 208.0 + s * (9.0 / 8.0))))));
+    return series / csqrt(A);
+}
+
+cplx oracle_rc(cplx x, cplx y) {
+    /* Cauchy principal value for real negative y (Sec. 2.2): the pole of the
+     * integrand is moved off the path with R_C(x,-q) = sqrt(x/(x+q)) R_C(x+q, q). */
+    if (cimag(y) == 0.0 && creal(y) < 0.0 && cimag(x) == 0.0 && creal(x) >= 0.0) {
+        double q = -creal(y);
+        return csqrt(x / (x + q)) * rc_dup(x + q, q);
+    }
+    return rc_dup(x, y);
+}
+
+/* R_F(x, y, z), eq. (2.6). */
+cplx oracle_rf(cplx x, cplx y, cplx z) {
+    cplx x0 = x, y0 = y, A0 = (x + y + z) / 3.0, A = A0;
+    double Q = pow(3.0 * CARLSON_R, -1.0 / 6.0) * maxabs3(A0 - x, A0 - y, A0 - z);
+    double f = 1.0;
+    int m = 0;
+    while (f * Q >= cabs(A) && m < CARLSON_MAXIT) {
+        cplx sx = csqrt(x), sy = csqrt(y), sz = csqrt(z);
+        cplx lam = sx * sy + sx * sz + sy * sz;
+        A = (A + lam) / 4.0; x = (x + lam) / 4.0; y = (y + lam) / 4.0; z = (z + lam) / 4.0;
+        f /= 4.0; m++;
+    }
+    cplx X = f * (A0 - x0) / A, Y = f * (A0 - y0) / A, Z = -(X + Y);
+    cplx E2 = X * Y - Z * Z, E3 = X * Y * Z;
+    cplx series = 1.0 - E2 / 10.0 + (g_mutation == 1 ? 0.0 : E3 / 14.0) + E2 * E2 / 24.0
+                  - 3.0 * E2 * E3 / 44.0;
+    return series / csqrt(A);
+}
+
+/* R_J(x, y, z, p) for p not on the negative real axis, eq. (2.7). */
+static cplx rj_dup(cplx x, cplx y, cplx z, cplx p) {
+    cplx x0 = x, y0 = y, z0 = z, A0 = (x + y + z + 2.0 * p) / 5.0, A = A0;
+    cplx delta = (p - x) * (p - y) * (p - z);
+    double Q = maxabs3(A0 - x, A0 - y, A0 - z);
+    if (cabs(A0 - p) > Q) Q = cabs(A0 - p);
+    Q *= pow(CARLSON_R / 4.0, -1.0 / 6.0);
+    double f = 1.0;
+    cplx sum = 0.0;
+    int m = 0;
+    while (f * Q >= cabs(A) && m < CARLSON_MAXIT) {
+        cplx sx = csqrt(x), sy = csqrt(y), sz = csqrt(z), sp = csqrt(p);
+        cplx lam = sx * sy + sx * sz + sy * sz;
+        cplx d = (sp + sx) * (sp + sy) * (sp + sz);
+        cplx e = f * f * f * delta / (d * d);
+        if (g_mutation == 6)
+            sum += f / d;
+        else
+            sum += f * rc_dup(1.0, 1.0 + e) / d;
+        A = (A + lam) / 4.0; x = (x + lam) / 4.0; y = (y + lam) / 4.0; z = (z + lam) / 4.0;
+        p = (p + lam) / 4.0;
+        f /= 4.0; m++;
+    }
+    cplx X = f * (A0 - x0) / A, Y = f * (A0 - y0) / A, Z = f * (A0 - z0) / A;
+    cplx P = -(X + Y + Z) / 2.0;
+    cplx E2 = X * Y + X * Z + Y * Z - 3.0 * P * P;
+    cplx E3 = X * Y * Z + 2.0 * E2 * P + 4.0 * P * P * P;
+    cplx E4 = (2.0 * X * Y * Z + E2 * P + 3.0 * P * P * P) * P;
+    cplx E5 = X * Y * Z * P * P;
+    cplx series = 1.0 - 3.0 * E2 / 14.0 + E3 / 6.0 + 9.0 * E2 * E2 / 88.0 - 3.0 * E4 / 22.0
+                  - 9.0 * E2 * E3 / 52.0 + 3.0 * E5 / 26.0;
+    return f * series / (A * csqrt(A)) + 6.0 * sum;
+}
+
+static int is_real(cplx v) { return cimag(v) == 0.0; }
+
+/* R_J with the Cauchy principal value for real negative p (Sec. 2.2).
+ * The triple must then be real-valued as a set (three reals, or one real and
+ * a conjugate pair); the real member goes to the third slot and
+ *   (q+z) R_J(x,y,z,-q) = (s-z) R_J(x,y,z,s) - 3 R_F(x,y,z)
+ *                         + 3 sqrt(xyz/(xy+sq)) R_C(xy+sq, sq),
+ *   s = (z(x+y+q) - xy)/(z+q),
+ * which is only used when s > 0 (otherwise NaN is returned). */
+cplx oracle_rj(cplx x, cplx y, cplx z, cplx p) {
+    if (!(is_real(p) && creal(p) < 0.0)) return rj_dup(x, y, z, p);
+    cplx v[3] = {x, y, z};
+    int ir = -1;
+    for (int i = 0; i < 3; i++)
+        if (is_real(v[i]) && (ir < 0 || creal(v[i]) > creal(v[ir]))) ir = i;
+    if (ir < 0) return NAN;
+    cplx zz = v[ir], xx = v[(ir + 1) % 3], yy = v[(ir + 2) % 3];
+    double q = -creal(p);
+    cplx s = (zz * (xx + yy + q) - xx * yy) / (zz + q);
+    if (!(creal(s) > 0.0)) return NAN;
+    cplx xy = xx * yy;
+    cplx val = (s - zz) * rj_dup(xx, yy, zz, s) - 3.0 * oracle_rf(xx, yy, zz)
+               + 3.0 * csqrt(xx * yy * zz / (xy + s * q)) * oracle_rc(xy + s * q, s * q);
+    return val / (q + zz);
+}
+
+/* R_D(x, y, z) = R_J(x, y, z, z), eq. (2.9). */
+cplx oracle_rd(cplx x, cplx y, cplx z) { return rj_dup(x, y, z, z); }
+
+/* Batch entry for tests: kind 0=R_F 1=R_J 2=R_C 3=R_D; args [n][4] complex as
+ * (re,im) pairs; out [n] complex as (re,im). */
+void oracle_carlson_batch(int kind, int64_t n, const double* args, double* out) {
+    for (int64_t i = 0; i < n; i++) {
+        const double* a = args + 8 * i;
+        cplx x = a[0] + I * a[1], y = a[2] + I * a[3], z = a[4] + I * a[5], p = a[6] + I * a[7];
+        cplx r = 0;
+        switch (kind) {
+            case 0: r = oracle_rf(x, y, z); break;
+            case 1: r = oracle_rj(x, y, z, p); break;
+            case 2: r = oracle_rc(x, y); break;
+            case 3: r = oracle_rd(x, y, z); break;
+            default: r = NAN;
+        }
+        out[2 * i] = creal(r);
+        out[2 * i + 1] = cimag(r);
+    }
+}
+
+/* ======================================================================== */
+/* Curvature map and observables (Sec. 2.1.1; ref. [59] eqs. 13.47, 13.57;  */
+/* distance modulus fn22).                                                  */
+/* ======================================================================== */
+
+/* S_k(D) for dimensionless comoving distance D and curvature Ok, together
+ * with dS/dD and dS/dOk. */
+static void curv_map(double D, double Ok, double* S, double* SD, double* Sk) {
+    double u = Ok * D * D;
+    if (fabs(u) < 1e-2) {
+        /* Taylor series in u = Ok D^2 (exact to double precision here). */
+        double s = 0, sd = 0, sk = 0, term = 1.0, fact = 1.0;
+        for (int n = 0; n < 9; n++) {
+            /* S = D sum u^n/(2n+1)!, S_D = sum u^n/(2n)!, S_k = D^3 sum n u^(n-1)/(2n+1)! */
+            double f2n1 = fact * (2 * n + 1);      /* (2n+1)! */
+            s += D * term / f2n1;
+            sd += term / fact;                     /* fact = (2n)! */
+            if (n > 0) sk += D * D * D * n * (term / u) / f2n1;
+            term *= u;
+            fact *= (2 * n + 1) * (2 * n + 2);
+        }
+        if (u == 0.0) sk = D * D * D / 6.0;
+        *S = s; *SD = sd; *Sk = sk;
+        return;
+    }
+    if (Ok > 0) {
+        double r = sqrt(Ok);
+        *S = sinh(r * D) / r;
+        *SD = cosh(r * D);
+    } else {
+        double r = sqrt(-Ok);
+        *S = sin(r * D) / r;
+        *SD = cos(r * D);
+    }
+    *Sk = (D * (*SD) - *S) / (2.0 * Ok);
+}
+
+/* ======================================================================== */
+/* O1 / O4: adaptive Gauss-Legendre quadrature in the scale factor.         */
+/*   chi = (c/H0) int_a^1 da / sqrt(Q(a)),                                  */
+/*   t   = (1/H0) int_a^1 a da / sqrt(Q(a)),                                */
+/*   X   = (c/H0) int_a^1 a^-2 da / sqrt(Q(a)),                             */
+/* with Q(a) = Or + Om a + Ok a^2 + OL a^4 = a^4 E^2(z), a = 1/(1+z); this  */
+/* is eqs. (2.3)-(2.5) after dz = -da/a^2.                                  */
+/* ======================================================================== */
+#define NGL 15
+static double gl_x[NGL], gl_w[NGL];
+static int gl_ready = 0;
+
+static void gl_init(void) {
+    /* Gauss-Legendre nodes: Newton iteration on the Legendre polynomial P_n. */
+    const int n = NGL;
+    for (int i = 0; i < n; i++) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; it++) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; k++) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1; p1 = p2;
+            }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-17) break;
+        }
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; k++) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1; p1 = p2;
+        }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        gl_x[i] = x;
+        gl_w[i] = 2.0 / ((1.0 - x * x) * dp * dp);
+    }
+    gl_ready = 1;
+}
+
+#define NCOMP 15 /* 3 forward integrands + 3 weights x 4 parameter directions */
+
+typedef struct { double Om, OL, Or, Ok; } cosmo_t;
+
+/* Integrand vector at scale factor a.
+ * [0..2]: w(a)/sqrt(Q) for w = 1, a, a^-2.
+ * [3 + 4*iw + ig]: -(1/2) w(a) g(a) Q^-3/2 for g = dQ/dOm = a, dQ/dOL = a^4,
+ *                  dQ/dOr = 1, dQ/dOk = a^2 (Leibniz rule under the integral). */
+static void integrand(double a, const cosmo_t* c, double* out) {
+    double Q = c->Or + c->Om * a + c->Ok * a * a + c->OL * a * a * a * a;
+    double iq = 1.0 / sqrt(Q), iq3 = iq / Q;
+    double w[3] = {1.0, a, 1.0 / (a * a)};
+    double g[4] = {a, a * a * a * a, 1.0, a * a};
+    for (int iw = 0; iw < 3; iw++) {
+        out[iw] = w[iw] * iq;
+        for (int ig = 0; ig < 4; ig++) out[3 + 4 * iw + ig] = -0.5 * w[iw] * g[ig] * iq3;
+    }
+}
+
+/* 15-point rule on [lo, hi] of the variable t; the scale factor is a = t
+ * (mode 0) or a = 1 - t (mode 1, used next to a = 1 so that the width of a
+ * short interval z/(1+z) is exact). */
+static void gl_rule(const cosmo_t* c, int mode, double lo, double hi, double* res, double* absres) {
+    double h = 0.5 * (hi - lo), mid = 0.5 * (hi + lo), v[NCOMP];
+    for (int k = 0; k < NCOMP; k++) { res[k] = 0; if (absres) absres[k] = 0; }
+    for (int i = 0; i < NGL; i++) {
+        double tt = mid + h * gl_x[i];
+        integrand(mode ? 1.0 - tt : tt, c, v);
+        for (int k = 0; k < NCOMP; k++) {
+            res[k] += gl_w[i] * h * v[k];
+            if (absres) absres[k] += gl_w[i] * h * fabs(v[k]);
+        }
+    }
+}
+
+/* Adaptive bisection: an interval is accepted when, for every component,
+ * the 15-point rule on it and the sum over its two halves agree to rtol times
+ * the interval's own integral of |f| (so the total relative error is at most
+ * about rtol).  At most MAX_INTERVALS intervals are evaluated; the return
+ * value is the number of accepted intervals, negative if the cap was hit. */
+#define MAX_INTERVALS 200000
+static int adapt(const cosmo_t* c, int mode, double lo, double hi, double rtol, double* total) {
+    double whole[NCOMP], wabs[NCOMP];
+    gl_rule(c, mode, lo, hi, whole, wabs);
+    for (int k = 0; k < NCOMP; k++) total[k] = 0;
+    static double stk_lo[256], stk_hi[256], stk_v[256][NCOMP];
+    int sp = 0, nacc = 0, nev = 0, capped = 0;
+    stk_lo[0] = lo; stk_hi[0] = hi;
+    memcpy(stk_v[0], whole, sizeof(whole));
+    sp = 1;
+    while (sp > 0) {
+        sp--;
+        double a = stk_lo[sp], b = stk_hi[sp], m = 0.5 * (a + b);
+        double I1[NCOMP], L[NCOMP], R[NCOMP], La[NCOMP], Ra[NCOMP];
+        memcpy(I1, stk_v[sp], sizeof(I1));
+        gl_rule(c, mode, a, m, L, La);
+        gl_rule(c, mode, m, b, R, Ra);
+        nev++;
+        int ok = 1;
+        for (int k = 0; k < NCOMP; k++) {
+            double err = fabs(L[k] + R[k] - I1[k]);
+            if (err > rtol * (La[k] + Ra[k]) && err > 1e-300) { ok = 0; break; }
+        }
+        if (nev > MAX_INTERVALS) capped = 1;
+        if (ok || capped || sp >= 250 || (b - a) < 1e-15 * (hi - lo)) {
+            for (int k = 0; k < NCOMP; k++) total[k] += L[k] + R[k];
+            nacc++;
+        } else {
+            stk_lo[sp] = m; stk_hi[sp] = b; memcpy(stk_v[sp], R, sizeof(R)); sp++;
+            stk_lo[sp] = a; stk_hi[sp] = m; memcpy(stk_v[sp], L, sizeof(L)); sp++;
+        }
+    }
+    return capped ? -nacc : nacc;
+}
+
+static void unpack_params(const double* p, int ncol, double* H0, cosmo_t* c) {
+    *H0 = p[0];
+    c->Om = p[1]; c->OL = p[2]; c->Or = p[3];
+    c->Ok = (ncol >= 5) ? p[4] : 1.0 - p[1] - p[2] - p[3];
+}
+
+/* Row of pair j in a CSR batch (offsets == NULL: every row holds nnz/B). */
+static int64_t row_of(const int64_t* offsets, int64_t B, int64_t nnz, int64_t j) {
+    if (!offsets) return j / (nnz / B);
+    int64_t lo = 0, hi = B; /* offsets[lo] <= j < offsets[hi] */
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) / 2;
+        if (offsets[mid] <= j) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+/* O1 (+ O4 when jac != NULL).
+ * params [B][ncol] = (H0, Om, OL, Or[, Ok]); z [nnz]; rows by offsets.
+ * out [nnz][6] = (d_C, t, X, d_M, d_L, mu) in Mpc / Gyr / mag.
+ * jac [nnz][6][ncol]: d out / d params (H0 first).
+ * Returns 0 on success. */
+int oracle_quad_distances(const double* params, int64_t B, int ncol, const int64_t* offsets,
+                          const double* z, int64_t nnz, double rtol, double* out, double* jac) {
+    if (!gl_ready) gl_init();
+    for (int64_t j = 0; j < nnz; j++) {
+        int64_t b = row_of(offsets, B, nnz, j);
+        double H0;
+        cosmo_t c;
+        unpack_params(params + b * ncol, ncol, &H0, &c);
+        double zz = z[j], DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0;
+        double Iv[NCOMP];
+        if (zz == 0.0) {
+            for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
+        } else {
+            /* [a(z), 1] split at a = 1/2: near a = 1 integrate in s = 1 - a over
+             * [0, min(z/(1+z), 1/2)]; below a = 1/2 integrate in a itself. */
+            double w = zz / (1.0 + zz), I2[NCOMP];
+            adapt(&c, 1, 0.0, w < 0.5 ? w : 0.5, rtol, Iv);
+            if (w > 0.5) {
+                adapt(&c, 0, 1.0 / (1.0 + zz), 0.5, rtol, I2);
+                for (int k = 0; k < NCOMP; k++) Iv[k] += I2[k];
+            }
+        }
+        double S, SD, Sk;
+        curv_map(Iv[0], c.Ok, &S, &SD, &Sk);
+        double dC = DH * Iv[0], t = tH * Iv[1], X = DH * Iv[2], dM = DH * S;
+        double dL = (g_mutation == 4 ? 1.0 : 1.0 + zz) * dM;
+        double mu = 5.0 * log10(dL) + 25.0;
+        double* o = out + 6 * j;
+        o[0] = dC; o[1] = t; o[2] = X; o[3] = dM; o[4] = dL; o[5] = mu;
+        if (!jac) continue;
+        double* J = jac + 6 * ncol * j;
+        /* H0: every distance and time scales as 1/H0. */
+        for (int k = 0; k < 5; k++) J[k * ncol + 0] = -o[k] / H0;
+        J[5 * ncol + 0] = -5.0 / (log(10.0) * H0);
+        /* Omega directions: dI_w/dtheta = sum_g (dQ/dtheta)_g-coefficients x J_w[g]. */
+        for (int ip = 1; ip < ncol; ip++) {
+            /* coefficients of (a, a^4, 1, a^2) in dQ/dtheta, and dOk/dtheta */
+            double cg[4] = {0, 0, 0, 0}, dOk = 0;
+            if (ip == 1) cg[0] = 1;
+            if (ip == 2) cg[1] = 1;
+            if (ip == 3) cg[2] = 1;
+            if (ip == 4) cg[3] = 1;
+            if (ncol == 4) { /* closure: Ok = 1 - Om - OL - Or */
+                if (!(g_mutation == 5 && ip == 1)) cg[3] = -1;
+                dOk = -1;
+            } else if (ip == 4) {
+                dOk = 1;
+            }
+            double dI[3];
+            for (int iw = 0; iw < 3; iw++) {
+                dI[iw] = 0;
+                for (int ig = 0; ig < 4; ig++) dI[iw] += cg[ig] * Iv[3 + 4 * iw + ig];
+            }
+            double ddM = DH * (SD * dI[0] + Sk * dOk);
+            J[0 * ncol + ip] = DH * dI[0];
+            J[1 * ncol + ip] = tH * dI[1];
+            J[2 * ncol + ip] = DH * dI[2];
+            J[3 * ncol + ip] = ddM;
+            J[4 * ncol + ip] = (1.0 + zz) * ddM;
+            J[5 * ncol + ip] = (zz == 0.0) ? 0.0 : 5.0 / log(10.0) * ddM / dM;
+        }
+    }
+    return 0;
+}
+
+/* ======================================================================== */
+/* O2: Carlson formulas (3.7)-(3.9) and (B.1)-(B.3), z1 = 0, z2 = z.        */
+/* ======================================================================== */
+
+/* Quartic, eqs. (3.7)-(3.9).  r[4]: roots of E^2 in z.  it: index i for t;
+ * (iX, lX): indices i and l for X; the remaining two are j, k.  Outputs
+ * chi, t, X in units of c/H0, 1/H0, c/H0 with the Or^-1/2 prefactor
+ * included; im[3] receives the imaginary parts (should vanish). */
+static void quartic_carlson(const cplx* r, double Or, double z, int it, int iX, int lX,
+                            double* res, double* im) {
+    cplx X[4], Y[4];
+    for (int m = 0; m < 4; m++) {
+        X[m] = csqrt(z - r[m]);
+        Y[m] = csqrt(-r[m]);
+        if (g_mutation == 3) { cplx s = X[m]; X[m] = Y[m]; Y[m] = s; }
+    }
+    /* u_ab = X_a X_b Y_c Y_d + Y_a Y_b X_c X_d, {c,d} the complement of {a,b} */
+#define UAB(a, b, out) do { int cc_ = -1, dd_ = -1; \
+        for (int m_ = 0; m_ < 4; m_++) if (m_ != (a) && m_ != (b)) { if (cc_ < 0) cc_ = m_; else dd_ = m_; } \
+        out = X[a] * X[b] * Y[cc_] * Y[dd_] + Y[a] * Y[b] * X[cc_] * X[dd_]; } while (0)
+    cplx Ut[3];
+    double Or_h = 1.0 / sqrt(Or);
+    /* ---- chi, eq. (3.7): R_F of (u_12^2, u_13^2, u_14^2) ---- */
+    cplx u12, u13, u14;
+    UAB(0, 1, u12); UAB(0, 2, u13); UAB(0, 3, u14);
+    cplx rf = oracle_rf(u12 * u12, u13 * u13, u14 * u14);
+    cplx chi = Or_h * 2.0 * z * rf;
+    /* ---- t, eq. (3.8), with the index i = it ---- */
+    {
+        int i = it, o[3], n = 0;
+        for (int m = 0; m < 4; m++) if (m != i) o[n++] = m;
+        int j = o[0], k = o[1], l = o[2];
+        cplx uij, uik, uil;
+        UAB(i, j, uij); UAB(i, k, uik); UAB(i, l, uil);
+        Ut[0] = uij * uij; Ut[1] = uik * uik; Ut[2] = uil * uil;
+        cplx dij = r[j] - r[i], dik = r[k] - r[i], dil = r[l] - r[i];
+        cplx di5 = -(1.0 + r[i]), dj5 = -(1.0 + r[j]), dk5 = -(1.0 + r[k]), dl5 = -(1.0 + r[l]);
+        cplx ui5 = Ut[0] - z * z * dik * dil * dj5 / di5;
+        cplx qi5 = (1.0 + z) / ((-r[i]) * (z - r[i])) * ui5;
+        cplx si5 = qi5 + z * z * dk5 * dl5 * dj5 / di5;
+        if (fabs(cimag(ui5)) <= 1e-13 * cabs(ui5)) ui5 = creal(ui5);
+        if (fabs(cimag(qi5)) <= 1e-13 * cabs(qi5)) qi5 = creal(qi5);
+        if (fabs(cimag(si5)) <= 1e-13 * cabs(si5)) si5 = creal(si5);
+        cplx rfi = oracle_rf(Ut[0], Ut[1], Ut[2]);
+        cplx br = z * z / 3.0 * dij * dik * dil / di5 * oracle_rj(Ut[0], Ut[1], Ut[2], ui5)
+                  + (g_mutation == 2 ? -1.0 : 1.0) * oracle_rc(si5, qi5);
+        cplx t = Or_h * 2.0 * z / (r[i] + 1.0) * (rfi - br);
+        res[1] = creal(t); im[1] = cimag(t);
+    }
+    /* ---- X, eq. (3.9), with indices i = iX, l = lX ---- */
+    {
+        int i = iX, l = lX, o[2], n = 0;
+        for (int m = 0; m < 4; m++) if (m != i && m != l) o[n++] = m;
+        int j = o[0], k = o[1];
+        cplx uij, uik, uil;
+        UAB(i, j, uij); UAB(i, k, uik); UAB(i, l, uil);
+        cplx U0 = uij * uij, U1 = uik * uik, U2 = uil * uil;
+        cplx dij = r[j] - r[i], dik = r[k] - r[i], dil = r[l] - r[i];
+        cplx djl = r[l] - r[j], dkl = r[l] - r[k];
+        cplx ui0 = U0 - z * z * dik * dil;
+        cplx qi0 = ui0 / ((-r[i]) * (z - r[i]));
+        cplx si0 = qi0 + z * z;
+        if (fabs(cimag(ui0)) <= 1e-13 * cabs(ui0)) ui0 = creal(ui0);
+        if (fabs(cimag(qi0)) <= 1e-13 * cabs(qi0)) qi0 = creal(qi0);
+        if (fabs(cimag(si0)) <= 1e-13 * cabs(si0)) si0 = creal(si0);
+        cplx sumr = r[0] + r[1] + r[2] + r[3] + 4.0;
+        cplx rfx = oracle_rf(U0, U1, U2);
+        cplx term0 = (X[i] * X[j] * X[k] / X[l] - Y[i] * Y[j] * Y[k] / Y[l]) / z;
+        cplx term1 = (2.0 * (r[i] + 1.0) * (r[i] + 1.0) - dij * dik) * rfx;
+        cplx term2 = djl * dkl * (z * z / 3.0 * dij * dik * oracle_rd(U0, U1, U2)
+                                  + X[i] * Y[i] / (X[l] * Y[l]) / uil);
+        cplx term3 = sumr * (z * z / 3.0 * dij * dik * dil / (-1.0) * oracle_rj(U0, U1, U2, ui0)
+                             + oracle_rc(si0, qi0));
+        cplx Xd = Or_h * z * (term0 + term1 + term2 + term3);
+        res[2] = creal(Xd); im[2] = cimag(Xd);
+    }
+    res[0] = creal(chi); im[0] = cimag(chi);
+#undef UAB
+}
+
+/* Cubic (Or = 0), eqs. (B.1)-(B.3); r[3] roots of E^2 in z, i = index i. */
+static void cubic_carlson(const cplx* r, double Om, double z, int i, double* res, double* im) {
+    cplx X[3], Y[3];
+    for (int m = 0; m < 3; m++) {
+        X[m] = csqrt(z - r[m]);
+        Y[m] = csqrt(-r[m]);
+        if (g_mutation == 3) { cplx s = X[m]; X[m] = Y[m]; Y[m] = s; }
+    }
+    cplx u[3];
+    for (int a = 0; a < 3; a++) {
+        int b = (a + 1) % 3, c = (a + 2) % 3;
+        u[a] = X[a] * Y[b] * Y[c] + Y[a] * X[b] * X[c];
+    }
+    int j = (i + 1) % 3, k = (i + 2) % 3;
+    cplx U[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
+    double Om_h = 1.0 / sqrt(Om);
+    cplx rf = oracle_rf(U[0], U[1], U[2]);
+    cplx chi = Om_h * 2.0 * z * rf;
+    cplx ui5 = U[i] + z * z * (r[i] + 1.0);
+    cplx s5 = Y[0] * Y[1] * Y[2] * (z + 1.0) + X[0] * X[1] * X[2];
+    cplx qi5 = (1.0 + z) * ui5;
+    if (fabs(cimag(ui5)) <= 1e-13 * cabs(ui5)) ui5 = creal(ui5);
+    if (fabs(cimag(qi5)) <= 1e-13 * cabs(qi5)) qi5 = creal(qi5);
+    cplx s52 = s5 * s5;
+    if (fabs(cimag(s52)) <= 1e-13 * cabs(s52)) s52 = creal(s52);
+    cplx t = Om_h * 2.0 * z * (z * z / 3.0 * oracle_rj(U[0], U[1], U[2], ui5)
+                               + (g_mutation == 2 ? -1.0 : 1.0) * oracle_rc(s52, qi5));
+    cplx dij = r[j] - r[i], dik = r[k] - r[i];
+    cplx sumr = r[0] + r[1] + r[2] + 3.0;
+    cplx Xd = Om_h * 2.0 * z / 3.0 *
+              ((X[0] * X[1] * X[2] - Y[0] * Y[1] * Y[2]) / z
+               + (3.0 * (r[i] + 1.0) * (r[i] + 1.0) - dij * dik) * rf
+               + 2.0 * sumr * (z * z / 3.0 * dij * dik * oracle_rd(U[j], U[k], U[i])
+                               + Y[i] * X[i] / u[i]));
+    res[0] = creal(chi); im[0] = cimag(chi);
+    res[1] = creal(t); im[1] = cimag(t);
+    res[2] = creal(Xd); im[2] = cimag(Xd);
+}
+
+/* O2 batch.  roots [B][4] complex (re,im) of E^2 in x = 1+z (Sec. 3, eq. 3.2;
+ * m = nroot[b] = 4 or 3 entries used); perm [B][3] = (i_t, i_X, l_X).
+ * out [nnz][6] as in oracle_quad_distances; imag [nnz][3] imaginary parts. */
+int oracle_carlson_distances(const double* params, int64_t B, int ncol, const int64_t* offsets,
+                             const double* z, int64_t nnz, const double* roots,
+                             const int32_t* nroot, const int32_t* perm, double* out,
+                             double* imag) {
+    for (int64_t j = 0; j < nnz; j++) {
+        int64_t b = row_of(offsets, B, nnz, j);
+        double H0;
+        cosmo_t c;
+        unpack_params(params + b * ncol, ncol, &H0, &c);
+        double zz = z[j], DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0;
+        int m = nroot[b];
+        cplx r[4];
+        for (int a = 0; a < m; a++)
+            r[a] = (roots[8 * b + 2 * a] - 1.0) + I * roots[8 * b + 2 * a + 1];
+        double res[3] = {0, 0, 0}, im[3] = {0, 0, 0};
+        if (zz != 0.0) {
+            if (m == 4)
+                quartic_carlson(r, c.Or, zz, perm[3 * b], perm[3 * b + 1], perm[3 * b + 2], res, im);
+            else
+                cubic_carlson(r, c.Om, zz, perm[3 * b + 1], res, im);
+        }
+        double S, SD, Sk;
+        curv_map(res[0], c.Ok, &S, &SD, &Sk);
+        double* o = out + 6 * j;
+        o[0] = DH * res[0]; o[1] = tH * res[1]; o[2] = DH * res[2];
+        o[3] = DH * S;
+        o[4] = (g_mutation == 4 ? 1.0 : 1.0 + zz) * o[3];
+        o[5] = 5.0 * log10(o[4]) + 25.0;
+        if (imag) { imag[3 * j] = DH * im[0]; imag[3 * j + 1] = tH * im[1]; imag[3 * j + 2] = DH * im[2]; }
+    }
+    return 0;
+}
+
+/* Fine-grid composite Simpson rule of the same three integrals (brute force
+ * check for tiny inputs): n even subintervals on [1/(1+z), 1]. */
+int oracle_simpson(const double* p, int ncol, double z, int64_t n, double* res) {
+    double H0;
+    cosmo_t c;
+    unpack_params(p, ncol, &H0, &c);
+    double lo = 1.0 / (1.0 + z), h = (1.0 - lo) / n, s[3] = {0, 0, 0}, v[NCOMP];
+    for (int64_t i = 0; i <= n; i++) {
+        double w = (i == 0 || i == n) ? 1.0 : ((i & 1) ? 4.0 : 2.0);
+        integrand(lo + i * h, &c, v);
+        for (int k = 0; k < 3; k++) s[k] += w * v[k];
+    }
+    res[0] = C_KMS / H0 * s[0] * h / 3.0;
+    res[1] = HUBBLE_TIME_GYR / H0 * s[1] * h / 3.0;
+    res[2] = C_KMS / H0 * s[2] * h / 3.0;
+    return 0;
+}
