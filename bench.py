@@ -1,0 +1,310 @@
+"""Benchmark: distance+gradient pairs/s on the general LCDM+radiation+curvature
+batch (4096 cosmologies x 1024 redshifts, z ~ U(0, 10)).
+
+One step = one fused forward+adjoint pass of the whole path over the batch:
+FP64 root preparation per cosmology, then per pair the Carlson-integral
+distances d_C, t, X and mu (FP32, with the double-float island for X and the
+tangent of t), their tangents with respect to (H0, Om, OL, Or), and the
+per-cosmology FP64 reduction of the vector-Jacobian product with fixed random
+cotangents (lcdm_distances_vjp).
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle
+(adaptive quadrature forward + Leibniz-rule gradient) on a bounded sample.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "distance+gradient pairs/sec (FP32 batched) vs plain FP64 forward, same GB300, ≤2e-6 rel"
+UNIT = "pairs/s"
+OUTPUTS = ("d_C", "t", "X", "mu")
+# Algorithmic work of the dominant kernel per pair for this workload: FP32
+# floating-point operations (FFMA counted as 2) executed per pair, from the
+# ncu capture summarised in profiles/pairs_kernel_mix_k3_config2.md.
+FLOP_PER_PAIR = None
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def workload(seed_offset=0):
+    from paper_2212_01937_gb300 import workloads
+    b = workloads.config2(seed=2 + seed_offset)
+    return b
+
+
+def sample_clocks(stop, rows):
+    cmd = ["nvidia-smi", "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+           "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+           "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+           "--format=csv,noheader,nounits", "-lms", "200"]
+    try:
+        p = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+    except OSError:
+        return
+    def reader():
+        for line in p.stdout:
+            rows.append([x.strip() for x in line.split(",")])
+    t = threading.Thread(target=reader, daemon=True)
+    t.start()
+    stop.wait()
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    t.join(timeout=2)
+
+
+def clock_summary(rows, gpu_index):
+    sm, mx, reasons = [], 0.0, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for r in rows:
+        if len(r) < 9 or r[0] != str(gpu_index):
+            continue
+        try:
+            sm.append(float(r[1]))
+            mx = max(mx, float(r[2]))
+        except ValueError:
+            continue
+        for n, v in zip(names, r[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx or None,
+            "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_oracle_rate(b, budget_s, seed=0):
+    """Oracle (O1 quadrature + O4 Leibniz gradient) pairs/s on a random sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    def run(n):
+        idx = np.sort(rng.choice(b.nnz, n, replace=False))
+        rows = np.searchsorted(b.offsets, idx, side="right") - 1
+        z = b.z[idx].astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.quad_distances(b.params[rows], z, np.arange(n + 1), grad=True)
+        return time.perf_counter() - t0
+    t = run(2000)
+    n = int(min(max(2000, budget_s / max(t, 1e-9) * 2000), 2_000_000))
+    t = run(n)
+    return n / t, n
+
+
+def reference_arm(args):
+    """--impl reference: the FP64 CPU oracle timed on the host, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    b = workload()
+    rates = []
+    nsample = 0
+    for step in range(args.warmup + args.steps):
+        r, nsample = cpu_oracle_rate(b, budget_s=min(20.0, 60.0 / max(1, args.steps + args.warmup)), seed=step)
+        if step >= args.warmup:
+            rates.append(r)
+    v = float(np.mean(rates))
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b.nnz / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": b.name, "B": b.B, "n_per_row": 1024},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": "%d random pairs of the workload per step (adaptive quadrature "
+                                       "forward + Leibniz gradient, 1 thread)" % nsample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return reference_arm(args)
+
+    import torch
+    from paper_2212_01937_gb300 import lcdm
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    lcdm.load()
+
+    b = workload(seed_offset=rank)   # weak scaling: each rank owns a full batch of its own
+    B, npairs = b.B, b.nnz
+    params = torch.tensor(b.params, device=dev)
+    offsets = torch.tensor(b.offsets, device=dev)
+    z = torch.tensor(b.z, dtype=torch.float32, device=dev)
+    g = torch.Generator(device="cpu").manual_seed(7 + rank)
+    cot = {n: torch.randn(npairs, generator=g).to(dev) for n in OUTPUTS}
+    call = lcdm.Call(params, z, offsets, precision="fp32")
+    tune = lcdm.autotune(params, z, offsets, outputs=OUTPUTS, cot=cot, precision="fp32")
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+
+    def step():
+        return lcdm.distances_vjp(params, z, cot, offsets, outputs=OUTPUTS, precision="fp32",
+                                  workspace=call.ws)
+
+    def prep_only():
+        return lcdm.roots(params)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    launches0 = lcdm.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stop, rows = threading.Event(), []
+    th = threading.Thread(target=sample_clocks, args=(stop, rows), daemon=True)
+    th.start()
+    time.sleep(0.5)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        res = step()
+        ev[i][1].record()
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    stop.set()
+    th.join(timeout=10)
+    launches = lcdm.launch_count() - launches0
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = npairs * world / (ms / 1e3)
+
+    # prep share (FP64 root solve) timed alone, for the dominant-kernel duration
+    for _ in range(3):
+        prep_only()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(5):
+        prep_only()
+    e1.record()
+    torch.cuda.synchronize()
+    prep_ms = e0.elapsed_time(e1) / 5
+    pair_ms = max(ms - prep_ms, 1e-6)
+
+    # end to end through the public API with host buffers (pinned)
+    z_h = z.cpu().pin_memory()
+    cot_h = {n: v.cpu().pin_memory() for n, v in cot.items()}
+    outs_h = {n: torch.empty(npairs, dtype=torch.float32).pin_memory() for n in OUTPUTS}
+    grad_h = torch.empty(B, 4, dtype=torch.float64).pin_memory()
+    h2d = z_h.numel() * 4 + sum(v.numel() * 4 for v in cot_h.values())
+    d2h = sum(v.numel() * 4 for v in outs_h.values()) + grad_h.numel() * 8
+
+    def e2e_step():
+        zd = z_h.to(dev, non_blocking=True)
+        cd = {n: v.to(dev, non_blocking=True) for n, v in cot_h.items()}
+        r = lcdm.distances_vjp(params, zd, cd, offsets, outputs=OUTPUTS, precision="fp32", workspace=call.ws)
+        for n in OUTPUTS:
+            outs_h[n].copy_(r[n], non_blocking=True)
+        grad_h.copy_(r["grad"], non_blocking=True)
+
+    for _ in range(2):
+        e2e_step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record()
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1) / args.steps
+    e2e_value = npairs * world / (e2e_ms / 1e3)
+
+    line = None
+    if rank == 0:
+        clocks = clock_summary(rows, local)
+        achieved = None if FLOP_PER_PAIR is None else FLOP_PER_PAIR * npairs / (pair_ms / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "pairs_kernel<MIX,K=3,t,X>", "kernel_ms": pair_ms, "prep_ms": prep_ms,
+                "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, nominal clock)"}
+        extra = {}
+        if not args.no_fp64_baseline:
+            extra = fp64_baselines(lcdm, params, offsets, b, dev)
+        cpu = None
+        if not args.no_cpu_baseline:
+            r, n = cpu_oracle_rate(b, budget_s=12.0)
+            cpu = {"value": r, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": "%d random pairs of the workload, adaptive quadrature forward + Leibniz "
+                             "gradient, 1 thread" % n}
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": b.name + " (configs[1]: general LCDM+radiation+curvature batch)",
+                           "B": B, "n_per_row": 1024, "pairs_per_gpu": npairs, "outputs": list(OUTPUTS),
+                           "gradient": "fused VJP w.r.t. (H0, Om, OL, Or), random cotangents on all outputs",
+                           "precision": "FP32 pairs, FP64 roots and reductions, double-float X and dt",
+                           "l2": "flushed (256 MiB write) before every timed step",
+                           "launch": tune, "wall_s_timed": t_wall},
+                "gpu_launches": launches, "clocks": clocks, "roofline": roof,
+                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                        "ms_per_step": e2e_ms},
+                "cpu_baseline": cpu}
+        line.update(extra)
+        print(json.dumps(line))
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def fp64_baselines(lcdm, params, offsets, b, dev):
+    """The denominators named by the metric: the plain FP64 forward kernel
+    launched once per cosmology, and the same kernel batched."""
+    import torch
+    z64 = torch.tensor(b.z, dtype=torch.float64, device=dev)
+    n = b.offsets[1] - b.offsets[0]
+    ws = lcdm.Call(params[:1], z64[:n], layout="dense", precision="fp64", block=128, blocks_per_sm=1).ws
+    outs = ("d_C", "t", "X", "mu")
+
+    def plain():
+        for r in range(b.B):
+            lcdm.distances(params[r:r + 1], z64[r * n:(r + 1) * n], None, outputs=outs, layout="dense",
+                           precision="fp64", block=128, blocks_per_sm=1, workspace=ws)
+
+    def batched():
+        lcdm.distances(params, z64, offsets, outputs=outs, precision="fp64")
+
+    res = {}
+    for name, f, reps in (("plain_per_cosmology", plain, 1), ("batched", batched, 3)):
+        f()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        res[name] = {"value": b.nnz / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
+    return {"fp64_forward_baseline": res}
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,168 @@
+/*
+ * lcdm.h -- C ABI of liblcdm: LambdaCDM+radiation+curvature distances for many
+ * (cosmology, redshift) pairs on one GB300 (sm_103a), after Karchev,
+ * "Analytic auto-differentiable LambdaCDM cosmography" (arXiv:2212.01937).
+ *
+ * What is computed (z1 = 0, z2 = z for every pair):
+ *   comoving distance  d_C = chi(0, z)                eq. (2.3), via eq. (3.7)/(B.1)
+ *   time coordinate    t   = t(0, z) (lookback time)  eq. (2.4), via eq. (3.8)/(B.2)
+ *   absorption dist.   X   = d_abs(0, z)              eq. (2.5), via eq. (3.9)/(B.3)
+ *   transverse comoving distance d_M (curvature map), luminosity distance
+ *   d_L = (1+z) d_M and distance modulus mu = 5 log10(d_L / 10 pc)
+ *                                                       (Sec. 2.1.1; fn22)
+ * The quartic E^2 of eq. (2.2) is factorised per cosmology (eq. 3.2, FP64) and
+ * each integral is reduced to Carlson's R_F, R_J, R_D, R_C (eqs. 2.6-2.9),
+ * evaluated by duplication.  Derivatives with respect to the parameters use
+ * eqs. (2.10)-(2.12) and the root derivatives of App. A (eqs. A.1-A.4).
+ *
+ * Conventions shared by every entry point
+ *   params   [B][ncol] float64, row-major: (H0 [km/s/Mpc], Omega_m0,
+ *            Omega_L0, Omega_r0) with Omega_k0 = 1 - Om - OL - Or (closure,
+ *            Sec. 2.1) when ncol == 4, or a fifth column Omega_k0 (ncol == 5).
+ *            Omega_r0 == 0 selects the cubic formulas of App. B.1.
+ *   pairs    layout LCDM_LAYOUT_CSR: offsets[B+1] int64 (offsets[0] = 0,
+ *            non-decreasing, offsets[B] = n), z[n]; row b holds pairs
+ *            offsets[b] .. offsets[b+1]-1.  Empty rows are allowed.
+ *            LCDM_LAYOUT_DENSE: offsets ignored, every row holds n redshifts,
+ *            z[B*n].  LCDM_LAYOUT_SHARED: offsets ignored, all rows share the
+ *            n redshifts z[n]; pair (b, i) has index b*n + i.
+ *            npairs = n (CSR) or B*n (DENSE, SHARED).
+ *   dtype    precision LCDM_FP64: z, outputs, cotangents, Jacobians and
+ *            m_obs are float64.  LCDM_FP32_MIXED: they are float32; the root
+ *            solve and all per-cosmology reductions are FP64 and X (and the
+ *            tangent of t) is evaluated in double-float arithmetic.
+ *   units    d_C, d_M, d_L, X in Mpc; t in Gyr; mu in magnitudes.
+ *   memory   every pointer argument except opts is a DEVICE pointer owned by
+ *            the caller; the library allocates nothing.  Scratch comes from
+ *            the caller's workspace ws (>= lcdm_workspace_size bytes,
+ *            256-byte aligned) and must not be used concurrently by two calls.
+ *   streams  calls enqueue kernels on `stream` and return without
+ *            synchronising; results are ready when the stream reaches them.
+ *   errors   the return value reports argument and launch errors only
+ *            (LCDM_OK ... LCDM_ERR_UNSUPPORTED, see lcdm_status_string);
+ *            nothing is enqueued when an argument check fails.  Per-cosmology
+ *            problems are reported in cosmo_status[B] (int32, device):
+ *              0 ok
+ *              1 no Big Bang: a real root of E^2 at z >= 0 (Sec. 3, Fig. 1)
+ *              2 invalid parameters (non-finite, H0 <= 0, Omega_r0 < 0, or
+ *                Omega_m0 <= 0 when Omega_r0 == 0)
+ *              3 degenerate roots (coincident roots or rho_A == 0)
+ *              4 duplication did not converge / principal value not available
+ *              5 root configuration not supported (two complex pairs)
+ *            and every output of such a cosmology is NaN.
+ *   z = 0    gives d = t = X = 0, mu = -inf; tangents of mu with respect to
+ *            the Omega columns are 0 and d mu / d H0 = -5 / (H0 ln 10).
+ *   gradient with respect to Omega_r0 of a radiationless cosmology
+ *            (Omega_r0 == 0) is NaN: the cubic reduction has no such direction.
+ */
+#ifndef LCDM_H
+#define LCDM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LCDM_API_VERSION 1
+
+typedef enum {
+    LCDM_OK = 0,
+    LCDM_ERR_INVALID = 1,      /* bad argument: null pointer, size, layout, ncol ... */
+    LCDM_ERR_CUDA = 2,         /* a CUDA launch or query failed                     */
+    LCDM_ERR_WORKSPACE = 3,    /* workspace missing, too small or misaligned        */
+    LCDM_ERR_UNSUPPORTED = 4   /* combination not supported                         */
+} lcdm_status;
+
+enum { LCDM_FP64 = 0, LCDM_FP32_MIXED = 1 };
+enum { LCDM_LAYOUT_CSR = 0, LCDM_LAYOUT_DENSE = 1, LCDM_LAYOUT_SHARED = 2 };
+/* output slots (index into the out / jac / cot arrays) */
+enum { LCDM_DC = 0, LCDM_T = 1, LCDM_X = 2, LCDM_DM = 3, LCDM_DL = 4, LCDM_MU = 5, LCDM_NOUT = 6 };
+
+typedef struct {
+    int32_t ncol;           /* 4 (closure) or 5 (explicit Omega_k0)             */
+    int32_t precision;      /* LCDM_FP64 or LCDM_FP32_MIXED                      */
+    int32_t layout;         /* LCDM_LAYOUT_*                                     */
+    int32_t block;          /* threads per block (multiple of 32, <= 256); 0 = tuned */
+    int32_t blocks_per_sm;  /* persistent blocks per SM; 0 = tuned               */
+} lcdm_opts;
+
+/* Workspace bytes needed for B cosmologies (per-cosmology root records). */
+lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes);
+
+/* Root preparation alone (Sec. 3, eq. 3.2; App. A): roots of E^2 in z for
+ * each cosmology and their derivatives with respect to the Omega columns.
+ *   roots  [B][4][2] float64 (re, im): slot 0 = A, the real root with the
+ *          largest |1+r| (fn15), slot 1 = B (second real root; quartic only,
+ *          else -0), slots 2, 3 = the remaining pair (complex conjugates or two
+ *          reals).  May be NULL.
+ *   droots [B][4][2][ncol-1] float64, d root / d (Om, OL, Or[, Ok]); may be NULL.
+ *   kind   [B] int32: 0 quartic 2 real + pair, 1 quartic 4 real, 2 cubic 1 real
+ *          + pair, 3 cubic 3 real.  May be NULL.                               */
+lcdm_status lcdm_roots(const double* params, int64_t B, const lcdm_opts* opts, double* roots,
+                       double* droots, int32_t* kind, int32_t* cosmo_status, void* ws, size_t ws_bytes,
+                       cudaStream_t stream);
+
+/* Forward distances, eqs. (3.7)-(3.9) / (B.1)-(B.3) and the observables.
+ *   out[LCDM_NOUT]: per-output arrays [npairs]; NULL entries are not computed
+ *   (X costs most; leave it NULL when not needed).                          */
+lcdm_status lcdm_distances(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                           int64_t n, void* const out[LCDM_NOUT], int32_t* cosmo_status,
+                           const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Forward distances plus the per-pair Jacobian d out / d params (fused).
+ *   jac[LCDM_NOUT]: per-output arrays [npairs][ncol] (column 0 = H0); NULL
+ *   entries are skipped.  out may be NULL or contain NULL entries.          */
+lcdm_status lcdm_distances_jac(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                               int64_t n, void* const out[LCDM_NOUT], void* const jac[LCDM_NOUT],
+                               int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
+                               cudaStream_t stream);
+
+/* Vector-Jacobian product fused with the forward pass (the adjoint of the
+ * distance map): grad[b][c] = sum over pairs of row b and outputs o of
+ * cot[o][pair] * d out_o[pair] / d params[b][c].
+ *   cot[LCDM_NOUT]: cotangent arrays [npairs] (NULL = zero); out may be NULL.
+ *   grad [B][ncol] float64, overwritten (NaN rows for a bad cosmo_status). */
+lcdm_status lcdm_distances_vjp(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                               int64_t n, const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT],
+                               double* grad, int32_t* cosmo_status, const lcdm_opts* opts, void* ws,
+                               size_t ws_bytes, cudaStream_t stream);
+
+/* Gaussian log-likelihood of standardised magnitudes (Sec. 4):
+ *   loglike[b] = sum_i [ -(m_obs_i - mu(z_i; params_b) - M)^2 / (2 sigma^2)
+ *                        - ln(sigma sqrt(2 pi)) ]
+ * over the pairs of row b, and grad[b][c] = d loglike[b] / d params[b][c].
+ *   m_obs indexed like z (same layout); mu_out [npairs] optional.
+ *   loglike [B] float64 (required), grad [B][ncol] float64 (optional).
+ * The per-row sums are accumulated in FP64.                                */
+lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                               const void* m_obs, int64_t n, double M, double sigma, double* loglike,
+                               double* grad, void* mu_out, int32_t* cosmo_status, const lcdm_opts* opts,
+                               void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* Times the candidate launch shapes (threads per block x persistent blocks
+ * per SM) of the pair kernel on the given inputs, keeps the fastest in a
+ * process-wide cache keyed by (precision, outputs, tangents, layout, log2
+ * npairs) and returns it.  Arguments as lcdm_distances_vjp (cot and grad may
+ * be NULL for a forward-only shape; out entries are overwritten).  The call
+ * synchronises the stream; do not call it while capturing a CUDA graph.    */
+lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                          const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT], double* grad,
+                          int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
+                          cudaStream_t stream, int32_t* best_block, int32_t* best_blocks_per_sm,
+                          float* best_ms);
+
+/* Human-readable name of a lcdm_status value (static string). */
+const char* lcdm_status_string(int status);
+
+/* Number of kernels this library has launched in this process so far. */
+int64_t lcdm_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCDM_H */

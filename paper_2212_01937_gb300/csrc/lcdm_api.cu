@@ -1,0 +1,335 @@
+// Host side of liblcdm: argument checks, workspace carving, launch shapes,
+// the launch-shape autotuner, and the extern "C" entry points of include/lcdm.h.
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
+#include "../../include/lcdm.h"
+#include "lcdm_launch.cuh"
+#include "lcdm_prep.cuh"
+
+using namespace lcdm;
+
+namespace {
+
+std::atomic<int64_t> g_launches{0};
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+size_t ws_bytes_for(int64_t B) {
+    return align256((size_t)B * NREC * sizeof(double)) + align256((size_t)B * NREC * sizeof(float2));
+}
+
+bool opts_ok(const lcdm_opts* o) {
+    return o && (o->ncol == 4 || o->ncol == 5) && (o->precision == LCDM_FP64 || o->precision == LCDM_FP32_MIXED) &&
+           o->layout >= LCDM_LAYOUT_CSR && o->layout <= LCDM_LAYOUT_SHARED && o->block >= 0 && o->block <= 256 &&
+           (o->block % 32) == 0 && o->blocks_per_sm >= 0 && o->blocks_per_sm <= 64;
+}
+
+struct Carved {
+    double* recD;
+    float2* recF;
+};
+
+lcdm_status carve(void* ws, size_t ws_bytes, int64_t B, Carved& c) {
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < ws_bytes_for(B)) return LCDM_ERR_WORKSPACE;
+    c.recD = (double*)ws;
+    c.recF = (float2*)((char*)ws + align256((size_t)B * NREC * sizeof(double)));
+    return LCDM_OK;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+const PairsTable& table(int prec, int K) {
+    static PairsTable t[2][3];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        t[0][0] = table_f64_k0(); t[0][1] = table_f64_k3(); t[0][2] = table_f64_k4();
+        t[1][0] = table_mix_k0(); t[1][1] = table_mix_k3(); t[1][2] = table_mix_k4();
+    });
+    return t[prec][K == 0 ? 0 : (K == 3 ? 1 : 2)];
+}
+
+// tuned launch shapes: key (precision, K, WT, WX, layout, log2 npairs)
+typedef std::tuple<int, int, int, int, int, int> TuneKey;
+std::map<TuneKey, std::pair<int, int> > g_tuned;
+std::mutex g_tune_mu;
+
+int log2_bucket(int64_t n) {
+    int b = 0;
+    while (n > 1) { n >>= 1; b++; }
+    return b;
+}
+
+struct Plan {
+    PairArgs args;
+    int prec, K, wt, wx;
+    int64_t npairs;
+    TuneKey key;
+};
+
+lcdm_status check_pairs_args(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                             int32_t* status, const lcdm_opts* opts) {
+    if (!opts_ok(opts) || !params || !status || B <= 0 || n < 0) return LCDM_ERR_INVALID;
+    if (opts->layout == LCDM_LAYOUT_CSR && !offsets) return LCDM_ERR_INVALID;
+    if (n > 0 && !z) return LCDM_ERR_INVALID;
+    return LCDM_OK;
+}
+
+// Builds the kernel arguments; any of out / jac / cot / mobs may be null.
+lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                      void* const* out, void* const* jac, const void* const* cot, const void* mobs, double M,
+                      double sigma, double* grad, double* loglike, int32_t* status, const lcdm_opts* opts,
+                      const Carved& cv, Plan& P) {
+    PairArgs& a = P.args;
+    memset(&a, 0, sizeof(a));
+    a.recD = cv.recD;
+    a.recF = cv.recF;
+    a.status = status;
+    a.offsets = offsets;
+    a.z = z;
+    a.layout = opts->layout;
+    a.B = B;
+    a.ncol = opts->ncol;
+    a.nrow = n;
+    P.npairs = opts->layout == LCDM_LAYOUT_CSR ? n : B * n;
+    a.nnz = P.npairs;
+    bool tangents = grad != nullptr;
+    int wt = 0, wx = 0;
+    for (int i = 0; i < LCDM_NOUT; i++) {
+        a.out[i] = out ? out[i] : nullptr;
+        a.jac[i] = jac ? jac[i] : nullptr;
+        a.cot[i] = cot ? cot[i] : nullptr;
+        if (a.out[i]) a.outmask |= 1 << i;
+        if (a.jac[i]) tangents = true;
+        bool used = a.out[i] || a.jac[i] || a.cot[i];
+        if (used && i == LCDM_T) wt = 1;
+        if (used && i == LCDM_X) wx = 1;
+    }
+    if (mobs) { tangents = tangents || grad != nullptr; }
+    a.mobs = mobs;
+    a.M = M;
+    a.sigma = sigma;
+    a.grad = grad;
+    a.loglike = loglike;
+    P.prec = opts->precision == LCDM_FP64 ? 0 : 1;
+    P.K = tangents ? opts->ncol - 1 : 0;
+    P.wt = wt;
+    P.wx = wx;
+    P.key = TuneKey(P.prec, P.K, wt, wx, opts->layout, log2_bucket(P.npairs));
+    return LCDM_OK;
+}
+
+lcdm_status launch_plan(Plan& P, int block, int bps, cudaStream_t s) {
+    const PairsTable& t = table(P.prec, P.K);
+    int idx = (P.wt ? 2 : 0) + (P.wx ? 1 : 0);
+    if (block == 0 || bps == 0) {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(P.key);
+        if (it != g_tuned.end()) {
+            if (block == 0) block = it->second.first;
+            if (bps == 0) bps = it->second.second;
+        }
+    }
+    if (block == 0) block = 128;
+    int occ = t.occ[idx](block);
+    if (occ <= 0) return LCDM_ERR_CUDA;
+    if (bps == 0 || bps > occ) bps = occ;
+    int64_t warps = (int64_t)num_sms() * bps * (block / 32);
+    int64_t chunk = (P.npairs + warps - 1) / warps;
+    chunk = ((chunk + 31) / 32) * 32;
+    if (chunk < 32) chunk = 32;
+    P.args.chunk = chunk;
+    int64_t need_warps = (P.npairs + chunk - 1) / chunk;
+    int64_t grid = (need_warps * 32 + block - 1) / block;
+    if (grid < 1) grid = 1;
+    if (P.npairs == 0) return LCDM_OK;
+    cudaError_t e = t.launch[idx](P.args, (int)grid, block, s);
+    g_launches++;
+    return e == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
+}
+
+lcdm_status run_prep(const double* params, int64_t B, const lcdm_opts* opts, const Carved& cv, int32_t* status,
+                     double* grad, double* loglike, cudaStream_t s) {
+    int block = 128;
+    int64_t grid = (B + block - 1) / block;
+    prep_kernel<<<(unsigned)grid, block, 0, s>>>(params, B, opts->ncol, cv.recD, cv.recF, status, grad, loglike);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
+}
+
+__global__ void extract_roots(const double* __restrict__ recD, int64_t B, int ncol, double* roots, double* droots,
+                              int32_t* kind) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double* r = recD + b * NREC;
+    int kd = (int)r[RF_KIND];
+    bool cpair = kd == 0 || kd == 2, quartic = kd <= 1;
+    int K = ncol - 1;
+    if (kind) kind[b] = kd;
+    // slots: A, B, pair member 1, pair member 2
+    double re[4] = {r[RF_A], quartic ? r[RF_B] : -0.0, r[RF_PRE], cpair ? r[RF_PRE] : r[RF_PIM]};
+    double im[4] = {0, 0, cpair ? r[RF_PIM] : 0.0, cpair ? -r[RF_PIM] : 0.0};
+    if (roots)
+        for (int s = 0; s < 4; s++) { roots[(b * 4 + s) * 2] = re[s]; roots[(b * 4 + s) * 2 + 1] = im[s]; }
+    if (droots) {
+        for (int k = 0; k < K; k++) {
+            double dre[4] = {r[RF_DA + k], quartic ? r[RF_DB + k] : 0.0, r[RF_DPRE + k],
+                             cpair ? r[RF_DPRE + k] : r[RF_DPIM + k]};
+            double dim[4] = {0, 0, cpair ? r[RF_DPIM + k] : 0.0, cpair ? -r[RF_DPIM + k] : 0.0};
+            for (int s = 0; s < 4; s++) {
+                droots[((b * 4 + s) * 2 + 0) * K + k] = dre[s];
+                droots[((b * 4 + s) * 2 + 1) * K + k] = dim[s];
+            }
+        }
+    }
+}
+
+lcdm_status pairs_common(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                         void* const* out, void* const* jac, const void* const* cot, const void* mobs, double M,
+                         double sigma, double* grad, double* loglike, int32_t* status, const lcdm_opts* opts,
+                         void* ws, size_t ws_bytes, cudaStream_t stream) {
+    lcdm_status st = check_pairs_args(params, B, offsets, z, n, status, opts);
+    if (st != LCDM_OK) return st;
+    Carved cv;
+    st = carve(ws, ws_bytes, B, cv);
+    if (st != LCDM_OK) return st;
+    Plan P;
+    make_plan(params, B, offsets, z, n, out, jac, cot, mobs, M, sigma, grad, loglike, status, opts, cv, P);
+    st = run_prep(params, B, opts, cv, status, grad, loglike, stream);
+    if (st != LCDM_OK) return st;
+    return launch_plan(P, opts->block, opts->blocks_per_sm, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes) {
+    if (!opts_ok(opts) || B <= 0 || !bytes) return LCDM_ERR_INVALID;
+    *bytes = ws_bytes_for(B);
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_roots(const double* params, int64_t B, const lcdm_opts* opts, double* roots, double* droots,
+                       int32_t* kind, int32_t* cosmo_status, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!opts_ok(opts) || !params || !cosmo_status || B <= 0) return LCDM_ERR_INVALID;
+    Carved cv;
+    lcdm_status st = carve(ws, ws_bytes, B, cv);
+    if (st != LCDM_OK) return st;
+    st = run_prep(params, B, opts, cv, cosmo_status, nullptr, nullptr, stream);
+    if (st != LCDM_OK) return st;
+    extract_roots<<<(unsigned)((B + 127) / 128), 128, 0, stream>>>(cv.recD, B, opts->ncol, roots, droots, kind);
+    g_launches++;
+    return cudaGetLastError() == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
+}
+
+lcdm_status lcdm_distances(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                           void* const out[LCDM_NOUT], int32_t* cosmo_status, const lcdm_opts* opts, void* ws,
+                           size_t ws_bytes, cudaStream_t stream) {
+    if (!out) return LCDM_ERR_INVALID;
+    return pairs_common(params, B, offsets, z, n, out, nullptr, nullptr, nullptr, 0, 1, nullptr, nullptr,
+                        cosmo_status, opts, ws, ws_bytes, stream);
+}
+
+lcdm_status lcdm_distances_jac(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                               void* const out[LCDM_NOUT], void* const jac[LCDM_NOUT], int32_t* cosmo_status,
+                               const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!jac) return LCDM_ERR_INVALID;
+    return pairs_common(params, B, offsets, z, n, out, jac, nullptr, nullptr, 0, 1, nullptr, nullptr,
+                        cosmo_status, opts, ws, ws_bytes, stream);
+}
+
+lcdm_status lcdm_distances_vjp(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                               const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT], double* grad,
+                               int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
+                               cudaStream_t stream) {
+    if (!cot || !grad) return LCDM_ERR_INVALID;
+    return pairs_common(params, B, offsets, z, n, out, nullptr, cot, nullptr, 0, 1, grad, nullptr, cosmo_status,
+                        opts, ws, ws_bytes, stream);
+}
+
+lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                               const void* m_obs, int64_t n, double M, double sigma, double* loglike, double* grad,
+                               void* mu_out, int32_t* cosmo_status, const lcdm_opts* opts, void* ws,
+                               size_t ws_bytes, cudaStream_t stream) {
+    if (!m_obs || !loglike || !(sigma > 0) || !std::isfinite(M)) return LCDM_ERR_INVALID;
+    void* out[LCDM_NOUT] = {nullptr, nullptr, nullptr, nullptr, nullptr, mu_out};
+    return pairs_common(params, B, offsets, z, n, out, nullptr, nullptr, m_obs, M, sigma, grad, loglike,
+                        cosmo_status, opts, ws, ws_bytes, stream);
+}
+
+lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
+                          const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT], double* grad,
+                          int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
+                          cudaStream_t stream, int32_t* best_block, int32_t* best_bps, float* best_ms) {
+    lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
+    if (st != LCDM_OK) return st;
+    if ((cot == nullptr) != (grad == nullptr)) return LCDM_ERR_INVALID;
+    Carved cv;
+    st = carve(ws, ws_bytes, B, cv);
+    if (st != LCDM_OK) return st;
+    Plan P;
+    make_plan(params, B, offsets, z, n, out, nullptr, cot, nullptr, 0, 1, grad, nullptr, cosmo_status, opts, cv, P);
+    const PairsTable& t = table(P.prec, P.K);
+    int idx = (P.wt ? 2 : 0) + (P.wx ? 1 : 0);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LCDM_ERR_CUDA;
+    const int blocks[] = {64, 128, 256};
+    float best = 1e30f;
+    int bb = 128, bbps = 1;
+    for (int block : blocks) {
+        int occ = t.occ[idx](block);
+        for (int bps = 1; bps <= occ; bps *= 2) {
+            float tot = 0;
+            for (int rep = 0; rep < 3; rep++) {
+                if (run_prep(params, B, opts, cv, cosmo_status, grad, nullptr, stream) != LCDM_OK) return LCDM_ERR_CUDA;
+                cudaEventRecord(e0, stream);
+                if (launch_plan(P, block, bps, stream) != LCDM_OK) return LCDM_ERR_CUDA;
+                cudaEventRecord(e1, stream);
+                cudaEventSynchronize(e1);
+                float ms = 0;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep > 0) tot += ms;
+            }
+            tot /= 2;
+            if (tot < best) { best = tot; bb = block; bbps = bps; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[P.key] = std::make_pair(bb, bbps);
+    }
+    if (best_block) *best_block = bb;
+    if (best_bps) *best_bps = bbps;
+    if (best_ms) *best_ms = best;
+    return cudaGetLastError() == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
+}
+
+const char* lcdm_status_string(int s) {
+    switch (s) {
+        case LCDM_OK: return "LCDM_OK";
+        case LCDM_ERR_INVALID: return "LCDM_ERR_INVALID: invalid argument";
+        case LCDM_ERR_CUDA: return "LCDM_ERR_CUDA: CUDA launch or query failed";
+        case LCDM_ERR_WORKSPACE: return "LCDM_ERR_WORKSPACE: workspace missing, too small or not 256-byte aligned";
+        case LCDM_ERR_UNSUPPORTED: return "LCDM_ERR_UNSUPPORTED: unsupported combination";
+        default: return "unknown lcdm_status";
+    }
+}
+
+int64_t lcdm_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

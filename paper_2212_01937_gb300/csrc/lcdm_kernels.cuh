@@ -1,0 +1,439 @@
+// Kernels of the distance path:
+//   (the root preparation kernel is in lcdm_prep.cuh)
+//   pairs_kernel  persistent warps over contiguous ranges of (cosmology,
+//                 redshift) pairs: distance integrals (3.7)-(3.9) / (B.1)-(B.3),
+//                 observables, tangents, and the per-cosmology reductions of the
+//                 vector-Jacobian product and of the Gaussian log-likelihood.
+#pragma once
+#include <cuda_runtime.h>
+#include <math_constants.h>
+#include <stdint.h>
+
+#include <type_traits>
+
+#include "lcdm_dist.cuh"
+
+namespace lcdm {
+
+// Physical constants: speed of light [km/s]; Hubble time unit: 1 Mpc/km in Gyr.
+#define LCDM_C_KMS 299792.458
+#define LCDM_HUBBLE_GYR 977.7922216807891
+
+// ----------------------------------------------------------------------------
+// Per-cosmology record (FP64 master; a hi/lo float copy for the mixed path).
+// Roots are in z (r = rho - 1).  kind: 0 quartic, two real roots + conjugate
+// pair; 1 quartic, four real; 2 cubic, one real + pair; 3 cubic, three real.
+// For kinds 0/2 (P_re, P_im) is the pair member with positive imaginary part;
+// for kinds 1/3 they are the two real members.
+// ----------------------------------------------------------------------------
+enum RecField {
+    RF_A = 0, RF_B, RF_PRE, RF_PIM, RF_YA, RF_YB, RF_YPRE, RF_YPIM,
+    RF_AMH, RF_OK, RF_H0, RF_DH, RF_TH, RF_KIND,
+    RF_DA = 14, RF_DB = 18, RF_DPRE = 22, RF_DPIM = 26, RF_DAMH = 30, RF_DOK = 34,
+    NREC = 38
+};
+
+enum CosmoStatus {
+    ST_OK = 0, ST_NO_BIG_BANG = 1, ST_INVALID = 2, ST_DEGENERATE = 3, ST_NOCONV = 4, ST_UNSUPPORTED = 5
+};
+
+// ------------------------------------------------------------ observables ---
+// S_k(D): sinh / sin form, or its Taylor series in u = Ok D^2 near flatness,
+// with dS/dD and dS/dOk ([59] eqs. 13.47, 13.57 as cited in Sec. 2.1.1).
+template <class T> __device__ __forceinline__ void curv_map(T D, T Ok, T& S, T& SD, T& Sk) {
+    T u = Ok * D * D;
+    if (fabs(u) < (T)0.05) {
+        // coefficients 1/(2n+1)!, 1/(2n)!
+        const double cs[8] = {1.0, 1.0 / 6, 1.0 / 120, 1.0 / 5040, 1.0 / 362880, 1.0 / 39916800,
+                              1.0 / 6227020800.0, 1.0 / 1307674368000.0};
+        const double cd2[8] = {1.0, 0.5, 1.0 / 24, 1.0 / 720, 1.0 / 40320, 1.0 / 3628800,
+                               1.0 / 479001600.0, 1.0 / 87178291200.0};
+        T s = (T)cs[7], sd = (T)cd2[7], sk = (T)(7 * cs[7]);
+        for (int i = 6; i >= 0; i--) {
+            s = (T)cs[i] + u * s;
+            sd = (T)cd2[i] + u * sd;
+            if (i >= 1) sk = (T)(i * cs[i]) + u * sk;
+        }
+        S = D * s; SD = sd; Sk = D * D * D * sk;
+        return;
+    }
+    if (Ok > 0) {
+        T r = sqrt(Ok);
+        S = sinh(r * D) / r; SD = cosh(r * D);
+    } else {
+        T r = sqrt(-Ok);
+        S = sin(r * D) / r; SD = cos(r * D);
+    }
+    Sk = (D * SD - S) / (2 * Ok);
+}
+
+// ----------------------------------------------------------- pair kernel ----
+enum Layout { LAYOUT_CSR = 0, LAYOUT_DENSE = 1, LAYOUT_SHARED = 2 };
+enum Outputs { O_DC = 0, O_T = 1, O_X = 2, O_DM = 3, O_DL = 4, O_MU = 5, N_OUT = 6 };
+
+struct PairArgs {
+    const double* recD;
+    const float2* recF;
+    int32_t* status;
+    const int64_t* offsets;
+    const void* z;
+    int layout;
+    int64_t nrow;   // pairs per row (dense) / redshifts (shared)
+    int64_t nnz;
+    int64_t B;
+    int ncol;
+    int outmask;    // bit o: write out[o]
+    void* out[N_OUT];
+    void* jac[N_OUT];        // [nnz][ncol] per output, optional
+    const void* cot[N_OUT];  // cotangents for the VJP, optional
+    const void* mobs;        // loglike mode when non-null
+    double M, sigma;
+    double* grad;            // [B][ncol] accumulated (VJP or d loglike)
+    double* loglike;         // [B]
+    int64_t chunk;           // pairs per warp (multiple of 32)
+};
+
+template <class T> struct IO;
+template <> struct IO<float> { typedef float type; };
+template <> struct IO<double> { typedef double type; };
+
+// value of a record field in the pass type
+template <class T> __device__ __forceinline__ T recv(const double* rd, const float2* rf, int i);
+template <> __device__ __forceinline__ double recv<double>(const double* rd, const float2*, int i) { return rd[i]; }
+template <> __device__ __forceinline__ float recv<float>(const double*, const float2* rf, int i) { return rf[i].x; }
+template <> __device__ __forceinline__ df64 recv<df64>(const double*, const float2* rf, int i) {
+    float2 v = rf[i];
+    return mkdf(v.x, v.y);
+}
+
+// Build the root quantities in scalar S and evaluate the integrals.
+template <class T, int K, bool WT, bool WX> struct PairEval {
+    typedef typename std::conditional<(K > 0), Dual<T, K>, T>::type S;
+
+    static __device__ __forceinline__ S val(const double* rd, const float2* rf, int i, int di) {
+        S s;
+        if constexpr (K > 0) {
+            s.v = recv<T>(rd, rf, i);
+#pragma unroll
+            for (int k = 0; k < K; k++) s.d[k] = recv<T>(rd, rf, di + k);
+        } else {
+            s = recv<T>(rd, rf, i);
+        }
+        return s;
+    }
+    // Y = sqrt(-r) with its tangent -dr / (2Y)
+    static __device__ __forceinline__ S yval(const double* rd, const float2* rf, int iy, const S& r) {
+        S y;
+        if constexpr (K > 0) {
+            y.v = recv<T>(rd, rf, iy);
+            T h = cst<T>(-0.5) / y.v;
+#pragma unroll
+            for (int k = 0; k < K; k++) y.d[k] = r.d[k] * h;
+        } else {
+            y = recv<T>(rd, rf, iy);
+        }
+        return y;
+    }
+
+    static __device__ __forceinline__ void run(T z, const double* rd, const float2* rf, int kind, S& Ichi,
+                                               S& It, S& IX, int* fail) {
+        S A = val(rd, rf, RF_A, RF_DA);
+        S amh = val(rd, rf, RF_AMH, RF_DAMH);
+        S YA = yval(rd, rf, RF_YA, A);
+        S Pre = val(rd, rf, RF_PRE, RF_DPRE), Pim = val(rd, rf, RF_PIM, RF_DPIM);
+        if (kind == 0 || kind == 2) {
+            CPair<S> P = mkcp(mkcx<S>(Pre, Pim));
+            Cx<S> yv;
+            yv.re = val(rd, rf, RF_YPRE, RF_YPRE);
+            yv.im = val(rd, rf, RF_YPIM, RF_YPIM);
+            if constexpr (K > 0) {
+                // dY = -dP / (2Y), complex
+                Cx<T> y0 = mkcx<T>(yv.re.v, yv.im.v);
+                Cx<T> h = cxrcp(y0);
+#pragma unroll
+                for (int k = 0; k < K; k++) {
+                    Cx<T> dp = mkcx<T>(Pre.d[k], Pim.d[k]);
+                    Cx<T> dy = dp * h;
+                    yv.re.d[k] = dy.re * cst<T>(-0.5);
+                    yv.im.d[k] = dy.im * cst<T>(-0.5);
+                }
+            }
+            CPair<S> YP = mkcp(yv);
+            if (kind == 0) {
+                S B = val(rd, rf, RF_B, RF_DB);
+                S YB = yval(rd, rf, RF_YB, B);
+                quartic_integrals<S, CPair<S>, WT, WX>(z, A, B, P, YA, YB, YP, amh, Ichi, It, IX, fail);
+            } else {
+                cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, Ichi, It, IX, fail);
+            }
+        } else {
+            RPair<S> P = mkrp<S>(Pre, Pim);
+            RPair<S> YP = mkrp<S>(yval(rd, rf, RF_YPRE, Pre), yval(rd, rf, RF_YPIM, Pim));
+            if (kind == 1) {
+                S B = val(rd, rf, RF_B, RF_DB);
+                S YB = yval(rd, rf, RF_YB, B);
+                quartic_integrals<S, RPair<S>, WT, WX>(z, A, B, P, YA, YB, YP, amh, Ichi, It, IX, fail);
+            } else {
+                cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, Ichi, It, IX, fail);
+            }
+        }
+    }
+};
+
+__device__ __forceinline__ float to_io(float v, float) { return v; }
+__device__ __forceinline__ double to_io(double v, double) { return v; }
+__device__ __forceinline__ float to_io(df64 v, float) { return v.hi + v.lo; }
+
+// per-pair results in the output type TO
+template <class TO, int K> struct PairOut {
+    TO v[N_OUT];
+    TO d[N_OUT][K > 0 ? K : 1];   // tangents w.r.t. the Omega directions
+    TO h0[N_OUT];                 // derivative w.r.t. H0
+};
+
+template <class TO> __device__ __forceinline__ TO load_io(const void* p, int64_t i) {
+    return __ldg(reinterpret_cast<const TO*>(p) + i);
+}
+
+// Evaluate one pair.  PREC 0: FP64 throughout.  PREC 1: FP32, with a double-
+// float island whenever X or a tangent of t is requested.
+template <int PREC, int K, bool WT, bool WX>
+__device__ __forceinline__ void eval_pair(typename std::conditional<PREC == 0, double, float>::type zin,
+                                          const double* rd, const float2* rf, PairOut<
+                                          typename std::conditional<PREC == 0, double, float>::type, K>& o,
+                                          int* fail) {
+    typedef typename std::conditional<PREC == 0, double, float>::type TO;
+    const int kind = (int)rf[RF_KIND].x;
+    TO Ichi, It = 0, IX = 0;
+    TO dIchi[K > 0 ? K : 1], dIt[K > 0 ? K : 1], dIX[K > 0 ? K : 1];
+    const bool island = PREC == 1 && (WX || (WT && K > 0));
+    if constexpr (PREC == 0) {
+        typedef PairEval<double, K, WT, WX> E;
+        typename E::S a, b, c;
+        E::run(zin, rd, rf, kind, a, b, c, fail);
+        if constexpr (K > 0) {
+            Ichi = a.v; It = b.v; IX = c.v;
+            for (int k = 0; k < K; k++) { dIchi[k] = a.d[k]; dIt[k] = b.d[k]; dIX[k] = c.d[k]; }
+        } else {
+            Ichi = a; It = WT ? b : 0.0; IX = WX ? c : 0.0;
+        }
+    } else if (island) {
+        // one double-float variant per tangent count: t and X are both evaluated
+        typedef PairEval<df64, K, true, true> E;
+        typename E::S a, b, c;
+        E::run(mkdf(zin), rd, rf, kind, a, b, c, fail);
+        if constexpr (K > 0) {
+            Ichi = to_io(a.v, 0.f); It = to_io(b.v, 0.f); IX = to_io(c.v, 0.f);
+            for (int k = 0; k < K; k++) {
+                dIchi[k] = to_io(a.d[k], 0.f);
+                dIt[k] = to_io(b.d[k], 0.f);
+                dIX[k] = to_io(c.d[k], 0.f);
+            }
+        } else {
+            Ichi = to_io(a, 0.f); It = to_io(b, 0.f); IX = to_io(c, 0.f);
+        }
+    } else {
+        typedef PairEval<float, K, WT, false> E;
+        typename E::S a, b, c;
+        E::run(zin, rd, rf, kind, a, b, c, fail);
+        if constexpr (K > 0) {
+            Ichi = a.v;
+            for (int k = 0; k < K; k++) dIchi[k] = a.d[k];
+        } else {
+            Ichi = a; It = WT ? b : 0.f;
+        }
+    }
+    // observables
+    const TO z = zin;
+    const TO H0 = (TO)rd[RF_H0];
+    const TO DH = recv<TO>(rd, rf, RF_DH), tH = recv<TO>(rd, rf, RF_TH), Ok = recv<TO>(rd, rf, RF_OK);
+    TO S, SD, Sk;
+    curv_map<TO>(Ichi, Ok, S, SD, Sk);
+    const TO ln10 = (TO)2.302585092994045684;
+    o.v[O_DC] = DH * Ichi;
+    o.v[O_T] = tH * It;
+    o.v[O_X] = DH * IX;
+    o.v[O_DM] = DH * S;
+    o.v[O_DL] = ((TO)1 + z) * o.v[O_DM];
+    o.v[O_MU] = (TO)5 * log10(o.v[O_DL]) + (TO)25;
+    for (int i = 0; i < O_MU; i++) o.h0[i] = -o.v[i] / H0;
+    o.h0[O_MU] = (TO)-5 / (ln10 * H0);
+    if constexpr (K > 0) {
+        for (int k = 0; k < K; k++) {
+            TO dOk = recv<TO>(rd, rf, RF_DOK + k);
+            o.d[O_DC][k] = DH * dIchi[k];
+            o.d[O_T][k] = tH * dIt[k];
+            o.d[O_X][k] = DH * dIX[k];
+            o.d[O_DM][k] = DH * (SD * dIchi[k] + Sk * dOk);
+            o.d[O_DL][k] = ((TO)1 + z) * o.d[O_DM][k];
+            o.d[O_MU][k] = z == (TO)0 ? (TO)0 : (TO)5 / ln10 * o.d[O_DM][k] / o.v[O_DM];
+        }
+    }
+}
+
+// Warp-segmented sum of v[NV] by key (keys contiguous within the warp); the
+// first lane of each segment returns true and holds the segment total.
+template <int NV> __device__ __forceinline__ bool seg_reduce(double* v, int64_t key) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        int64_t ok = __shfl_down_sync(full, key, off);
+#pragma unroll
+        for (int i = 0; i < NV; i++) {
+            double o = __shfl_down_sync(full, v[i], off);
+            if (lane + off < 32 && ok == key) v[i] += o;
+        }
+    }
+    int64_t prev = __shfl_up_sync(full, key, 1);
+    return lane == 0 || prev != key;
+}
+
+__device__ __forceinline__ int64_t row_search(const int64_t* __restrict__ off, int64_t B, int64_t p) {
+    int64_t lo = 0, hi = B;  // off[lo] <= p < off[hi]
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (__ldg(off + mid) <= p) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ double acc_to_double(double v) { return v; }
+__device__ __forceinline__ double acc_to_double(df64 v) { return (double)v.hi + (double)v.lo; }
+
+// Warp sum of the per-lane accumulators of one row, added to the row's FP64 sums.
+template <int NV, int K, class AccT>
+__device__ __forceinline__ void flush_row(const AccT* acc, int64_t row, const PairArgs& a, int lane) {
+    double v[NV];
+#pragma unroll
+    for (int i = 0; i < NV; i++) {
+        v[i] = acc_to_double(acc[i]);
+        for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
+    }
+    if (lane == 0) {
+        if (a.grad) for (int i = 0; i < a.ncol; i++) atomicAdd(a.grad + row * a.ncol + i, v[i]);
+        if (a.loglike) atomicAdd(a.loglike + row, v[K + 1]);
+    }
+}
+
+template <int PREC, int K, bool WT, bool WX>
+__global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
+    typedef typename std::conditional<PREC == 0, double, float>::type TO;
+    constexpr int NV = K + 2;   // H0, K Omega directions, loglike value
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t start = warp * a.chunk;
+    if (start >= a.nnz) return;
+    const int64_t end = min(start + a.chunk, a.nnz);
+    const bool reduce = (a.grad != nullptr) || (a.loglike != nullptr);
+    const bool loglike = a.mobs != nullptr;
+    const TO inv_sig = (TO)(1.0 / a.sigma);
+    const TO lnorm = (TO)(-log(a.sigma * 2.5066282746310002));
+    typedef typename std::conditional<PREC == 0, double, df64>::type AccT;
+    int64_t row = -1;
+    AccT acc[NV];
+    int64_t acc_row = -1;
+#pragma unroll
+    for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
+    for (int64_t base = start; base < end; base += 32) {
+        const int64_t pidx = base + lane;
+        const bool active = pidx < end;
+        const int64_t pp = active ? pidx : end - 1;
+        int64_t zi = pp;
+        if (a.layout == LAYOUT_CSR) {
+            if (row < 0) {
+                row = row_search(a.offsets, a.B, pp);
+            } else {
+                int steps = 0;
+                while (row < a.B - 1 && __ldg(a.offsets + row + 1) <= pp && steps < 8) { row++; steps++; }
+                if (row < a.B - 1 && __ldg(a.offsets + row + 1) <= pp) row = row_search(a.offsets, a.B, pp);
+            }
+        } else {
+            row = pp / a.nrow;
+            if (a.layout == LAYOUT_SHARED) zi = pp - row * a.nrow;
+        }
+        const double* rd = a.recD + row * NREC;
+        const float2* rf = a.recF + row * NREC;
+        const int st = a.status[row];
+        const TO z = load_io<TO>(a.z, zi);
+        PairOut<TO, K> o;
+        int fail = 0;
+        if (st == ST_OK) {
+            if (z == (TO)0) {
+                for (int i = 0; i < N_OUT; i++) { o.v[i] = 0; o.h0[i] = 0; for (int k = 0; k < (K > 0 ? K : 1); k++) o.d[i][k] = 0; }
+                o.v[O_MU] = -CUDART_INF;
+                o.h0[O_MU] = (TO)(-5.0 / (2.302585092994045684 * rd[RF_H0]));
+            } else {
+                eval_pair<PREC, K, WT, WX>(z, rd, rf, o, &fail);
+            }
+        }
+        if (st != ST_OK || fail) {
+            const TO nan = (TO)CUDART_NAN;
+            for (int i = 0; i < N_OUT; i++) { o.v[i] = nan; o.h0[i] = nan; for (int k = 0; k < (K > 0 ? K : 1); k++) o.d[i][k] = nan; }
+            if (fail && active && st == ST_OK) atomicMax(a.status + row, (int)ST_NOCONV);
+        }
+        if (active) {
+#pragma unroll
+            for (int i = 0; i < N_OUT; i++) {
+                if (a.outmask & (1 << i)) reinterpret_cast<TO*>(a.out[i])[pidx] = o.v[i];
+                if (K > 0 && a.jac[i]) {
+                    TO* jp = reinterpret_cast<TO*>(a.jac[i]) + pidx * a.ncol;
+                    jp[0] = o.h0[i];
+                    for (int k = 0; k < K; k++) jp[1 + k] = o.d[i][k];
+                }
+            }
+        }
+        if (!reduce) continue;
+        // contribution of this pair to the per-cosmology sums
+        TO c[NV];
+#pragma unroll
+        for (int i = 0; i < NV; i++) c[i] = 0;
+        if (active && st == ST_OK && !fail) {
+            if (loglike) {
+                TO r = (load_io<TO>(a.mobs, zi) - o.v[O_MU] - (TO)a.M) * inv_sig;
+                TO w = r * inv_sig;
+                c[0] = w * o.h0[O_MU];
+#pragma unroll
+                for (int k = 0; k < K; k++) c[1 + k] = w * o.d[O_MU][k];
+                c[K + 1] = (TO)-0.5 * r * r + lnorm;
+            } else {
+#pragma unroll
+                for (int i = 0; i < N_OUT; i++) {
+                    if (!a.cot[i]) continue;
+                    TO g = load_io<TO>(a.cot[i], pidx);
+                    c[0] += g * o.h0[i];
+#pragma unroll
+                    for (int k = 0; k < K; k++) c[1 + k] += g * o.d[i][k];
+                }
+            }
+        }
+        // register accumulation while the whole warp stays on one row
+        const int64_t r0 = __shfl_sync(0xffffffffu, row, 0);
+        const bool uniform = __all_sync(0xffffffffu, row == r0);
+        if (uniform && r0 == acc_row) {
+#pragma unroll
+            for (int i = 0; i < NV; i++) acc[i] = acc[i] + c[i];
+            continue;
+        }
+        if (acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane);
+        if (uniform) {
+#pragma unroll
+            for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0) + c[i];
+            acc_row = r0;
+        } else {
+            double cd_[NV];
+#pragma unroll
+            for (int i = 0; i < NV; i++) cd_[i] = (double)c[i];
+            if (seg_reduce<NV>(cd_, row) && active) {
+                if (a.grad) for (int i = 0; i < a.ncol; i++) atomicAdd(a.grad + row * a.ncol + i, cd_[i]);
+                if (a.loglike) atomicAdd(a.loglike + row, cd_[K + 1]);
+            }
+#pragma unroll
+            for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
+            acc_row = -1;
+        }
+    }
+    if (reduce && acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane);
+}
+
+}  // namespace lcdm

@@ -1,0 +1,539 @@
+// Device arithmetic for the Carlson-integral distance path.
+//
+//  * df64        double-float numbers (an unevaluated sum of two floats,
+//                Dekker/Knuth error-free transformations).  On GB300 the FP64
+//                pipe issues about 1.6 DFMA per SM per clock against about
+//                115 FFMA, so the high-precision island of the mixed path is
+//                built on FP32 pairs instead of FP64.
+//  * Dual<T,K>   value + K tangents (forward mode over the density parameters).
+//  * Cx<S>       complex numbers over any scalar S.
+//  * CPair/RPair the two roots (or integral arguments) that are either a complex
+//                conjugate pair or two reals, with the operations the formulas
+//                need (sum and product of the members are real in both cases).
+//  * carlson_dup one duplication sequence on (x1, x2, x3) shared by R_F, the
+//                three R_D with each argument in turn as the special one, and up
+//                to two R_J tracks (eqs. 2.6-2.9), after Carlson's duplication
+//                algorithm (the paper's ref. [10]).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define LCDM_HD __device__ __forceinline__
+// heavy routines are real calls: each instantiation is optimised once
+#define LCDM_NI __device__ __noinline__
+
+namespace lcdm {
+
+// ---------------------------------------------------------------------------
+// df64
+// ---------------------------------------------------------------------------
+struct df64 {
+    float hi, lo;
+};
+LCDM_HD df64 mkdf(float h, float l = 0.f) { df64 r; r.hi = h; r.lo = l; return r; }
+LCDM_HD df64 df_from_double(double d) { float h = (float)d; return mkdf(h, (float)(d - (double)h)); }
+LCDM_HD double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
+// error-free sum (Knuth), sum with |a| >= |b| (Dekker), product via FMA
+LCDM_HD df64 two_sum(float a, float b) {
+    float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return mkdf(s, e);
+}
+LCDM_HD df64 fast_two_sum(float a, float b) {
+    float s = __fadd_rn(a, b);
+    return mkdf(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+LCDM_HD df64 operator+(df64 a, df64 b) {
+    df64 s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
+    s.lo = __fadd_rn(s.lo, t.hi);
+    s = fast_two_sum(s.hi, s.lo);
+    s.lo = __fadd_rn(s.lo, t.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
+LCDM_HD df64 operator-(df64 a) { return mkdf(-a.hi, -a.lo); }
+LCDM_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
+LCDM_HD df64 operator*(df64 a, df64 b) {
+    float p = __fmul_rn(a.hi, b.hi);
+    float e = fmaf(a.hi, b.hi, -p);
+    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+    return fast_two_sum(p, e);
+}
+LCDM_HD df64 operator/(df64 a, df64 b) {
+    float q1 = __fdiv_rn(a.hi, b.hi);
+    df64 r = a - b * mkdf(q1);
+    float q2 = __fdiv_rn(r.hi, b.hi);
+    r = r - b * mkdf(q2);
+    float q3 = __fdiv_rn(r.hi, b.hi);
+    df64 q = fast_two_sum(q1, q2);
+    return q + mkdf(q3);
+}
+LCDM_HD df64 operator+(df64 a, float b) { return a + mkdf(b); }
+LCDM_HD df64 operator-(df64 a, float b) { return a - mkdf(b); }
+LCDM_HD df64 operator*(df64 a, float b) {
+    float p = __fmul_rn(a.hi, b);
+    float e = fmaf(a.hi, b, -p);
+    e = fmaf(a.lo, b, e);
+    return fast_two_sum(p, e);
+}
+LCDM_HD df64 operator/(df64 a, float b) { return a / mkdf(b); }
+LCDM_HD df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
+LCDM_HD df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
+LCDM_HD df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
+// square root by one Newton-type correction of the float estimate (Karp)
+LCDM_HD df64 df_sqrt(df64 a) {
+    if (!(a.hi > 0.f)) return mkdf(a.hi == 0.f ? 0.f : __int_as_float(0x7fc00000));
+    float x = 1.0f / sqrtf(a.hi);
+    float y = __fmul_rn(a.hi, x);
+    float p = __fmul_rn(y, y);
+    df64 r = a - mkdf(p, fmaf(y, y, -p));
+    return fast_two_sum(y, r.hi * (0.5f * x));
+}
+
+// ---------------------------------------------------------------------------
+// Scalar traits: value used for branching, sqrt, abs, constants.
+// ---------------------------------------------------------------------------
+LCDM_HD float sval(float a) { return a; }
+LCDM_HD double sval(double a) { return a; }
+LCDM_HD float sval(df64 a) { return a.hi; }
+LCDM_HD float ssqrt(float a) { return sqrtf(a); }
+LCDM_HD double ssqrt(double a) { return sqrt(a); }
+LCDM_HD df64 ssqrt(df64 a) { return df_sqrt(a); }
+LCDM_HD float sabs(float a) { return fabsf(a); }
+LCDM_HD double sabs(double a) { return fabs(a); }
+LCDM_HD df64 sabs(df64 a) { return a.hi < 0.f ? -a : a; }
+template <class T> LCDM_HD T cst(double v);
+template <> LCDM_HD float cst<float>(double v) { return (float)v; }
+template <> LCDM_HD double cst<double>(double v) { return v; }
+template <> LCDM_HD df64 cst<df64>(double v) { return df_from_double(v); }
+// exact multiplication by 2^e
+LCDM_HD float sldexp(float a, int e) { return ldexpf(a, e); }
+LCDM_HD double sldexp(double a, int e) { return ldexp(a, e); }
+LCDM_HD df64 sldexp(df64 a, int e) { return mkdf(ldexpf(a.hi, e), ldexpf(a.lo, e)); }
+
+// ---------------------------------------------------------------------------
+// Dual numbers (forward-mode tangents over K parameters)
+// ---------------------------------------------------------------------------
+template <class T, int K>
+struct Dual {
+    T v;
+    T d[K];
+};
+template <class T, int K> LCDM_HD Dual<T, K> dconst(T v) {
+    Dual<T, K> r; r.v = v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = cst<T>(0.0);
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator+(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r; r.v = a.v + b.v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] + b.d[k];
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator-(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r; r.v = a.v - b.v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] - b.d[k];
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator-(const Dual<T, K>& a) {
+    Dual<T, K> r; r.v = -a.v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = -a.d[k];
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator*(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r; r.v = a.v * b.v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] * b.v + a.v * b.d[k];
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator/(const Dual<T, K>& a, const Dual<T, K>& b) {
+    Dual<T, K> r; T ib = cst<T>(1.0) / b.v; r.v = a.v * ib;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = (a.d[k] - r.v * b.d[k]) * ib;
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator+(const Dual<T, K>& a, T b) { Dual<T, K> r = a; r.v = a.v + b; return r; }
+template <class T, int K> LCDM_HD Dual<T, K> operator+(T b, const Dual<T, K>& a) { return a + b; }
+template <class T, int K> LCDM_HD Dual<T, K> operator-(const Dual<T, K>& a, T b) { Dual<T, K> r = a; r.v = a.v - b; return r; }
+template <class T, int K> LCDM_HD Dual<T, K> operator-(T b, const Dual<T, K>& a) { return (-a) + b; }
+template <class T, int K> LCDM_HD Dual<T, K> operator*(const Dual<T, K>& a, T b) {
+    Dual<T, K> r; r.v = a.v * b;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] * b;
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> operator*(T b, const Dual<T, K>& a) { return a * b; }
+template <class T, int K> LCDM_HD Dual<T, K> operator/(const Dual<T, K>& a, T b) { return a * (cst<T>(1.0) / b); }
+template <class T, int K> LCDM_HD Dual<T, K> operator/(T a, const Dual<T, K>& b) { return dconst<T, K>(a) / b; }
+template <class T, int K> LCDM_HD T sval(const Dual<T, K>& a) { return a.v; }
+template <class T, int K> LCDM_HD Dual<T, K> ssqrt(const Dual<T, K>& a) {
+    Dual<T, K> r; r.v = ssqrt(a.v);
+    T h = cst<T>(0.5) / r.v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] * h;
+    return r;
+}
+template <class T, int K> LCDM_HD Dual<T, K> sabs(const Dual<T, K>& a) { return sval(a.v) < 0 ? -a : a; }
+// value with a given gradient: r = v + sum_k g_k * (tangent_k of the inputs), built by callers
+template <class T, int K> LCDM_HD Dual<T, K> dlin(T v, T g, const Dual<T, K>& x) {
+    Dual<T, K> r; r.v = v;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = g * x.d[k];
+    return r;
+}
+template <class T, int K> LCDM_HD void dacc(Dual<T, K>& r, T g, const Dual<T, K>& x) {
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = r.d[k] + g * x.d[k];
+}
+// base scalar of a (possibly dual) scalar, and constants of that base type
+template <class S> struct Base { typedef S type; };
+template <class T, int K> struct Base<Dual<T, K> > { typedef T type; };
+template <class S> LCDM_HD typename Base<S>::type cst_like(const S&, double v) {
+    return cst<typename Base<S>::type>(v);
+}
+// plain scalars behave as duals with no tangent
+LCDM_HD float vof(float a) { return a; }
+LCDM_HD double vof(double a) { return a; }
+LCDM_HD df64 vof(df64 a) { return a; }
+template <class T, int K> LCDM_HD T vof(const Dual<T, K>& a) { return a.v; }
+
+// ---------------------------------------------------------------------------
+// Complex numbers over scalar S (S = T or Dual<T,K>)
+// ---------------------------------------------------------------------------
+template <class S>
+struct Cx {
+    S re, im;
+};
+template <class S> LCDM_HD Cx<S> mkcx(const S& r, const S& i) { Cx<S> c; c.re = r; c.im = i; return c; }
+template <class S> LCDM_HD Cx<S> operator+(const Cx<S>& a, const Cx<S>& b) { return mkcx<S>(a.re + b.re, a.im + b.im); }
+template <class S> LCDM_HD Cx<S> operator-(const Cx<S>& a, const Cx<S>& b) { return mkcx<S>(a.re - b.re, a.im - b.im); }
+template <class S> LCDM_HD Cx<S> operator-(const Cx<S>& a) { return mkcx<S>(-a.re, -a.im); }
+template <class S> LCDM_HD Cx<S> operator*(const Cx<S>& a, const Cx<S>& b) {
+    return mkcx<S>(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re);
+}
+template <class S> LCDM_HD Cx<S> operator/(const Cx<S>& a, const Cx<S>& b) {
+    S n = b.re * b.re + b.im * b.im;
+    return mkcx<S>((a.re * b.re + a.im * b.im) / n, (a.im * b.re - a.re * b.im) / n);
+}
+template <class S, class R> LCDM_HD Cx<S> cxadd(const Cx<S>& a, const R& s) { return mkcx<S>(a.re + s, a.im); }
+template <class S, class R> LCDM_HD Cx<S> cxrsub(const R& s, const Cx<S>& a) { return mkcx<S>(s - a.re, -a.im); }
+template <class S, class R> LCDM_HD Cx<S> cxscale(const Cx<S>& a, const R& s) { return mkcx<S>(a.re * s, a.im * s); }
+template <class S> LCDM_HD Cx<S> conj(const Cx<S>& a) { return mkcx<S>(a.re, -a.im); }
+template <class S> LCDM_HD S norm2(const Cx<S>& a) { return a.re * a.re + a.im * a.im; }
+template <class S> LCDM_HD Cx<S> cxrcp(const Cx<S>& a) {
+    S n = a.re * a.re + a.im * a.im;
+    S in = cst_like(n, 1.0) / n;
+    return mkcx<S>(a.re * in, -(a.im * in));
+}
+// principal square root
+template <class S> LCDM_HD Cx<S> cxsqrt(const Cx<S>& a) {
+    S r = ssqrt(a.re * a.re + a.im * a.im);
+    bool neg_im = sval(vof(a.im)) < 0;
+    if (sval(vof(a.re)) >= 0) {
+        S t = ssqrt((r + a.re) * cst_like(r, 0.5));
+        return mkcx<S>(t, a.im / (t + t));
+    }
+    S t = ssqrt((r - a.re) * cst_like(r, 0.5));
+    S ai = neg_im ? -a.im : a.im;
+    return mkcx<S>(ai / (t + t), neg_im ? -t : t);
+}
+
+// ---------------------------------------------------------------------------
+// Root / argument pairs.  A pair is two numbers that are either complex
+// conjugates (CPair, stores the first member) or two reals (RPair).
+// ---------------------------------------------------------------------------
+template <class S> struct CPair { Cx<S> c; };
+template <class S> struct RPair { S a, b; };
+
+template <class S> LCDM_HD CPair<S> mkcp(const Cx<S>& c) { CPair<S> p; p.c = c; return p; }
+template <class S> LCDM_HD RPair<S> mkrp(const S& a, const S& b) { RPair<S> p; p.a = a; p.b = b; return p; }
+
+// sum and product of the two members (real in both cases)
+template <class S> LCDM_HD S psum(const CPair<S>& p) { return p.c.re + p.c.re; }
+template <class S> LCDM_HD S psum(const RPair<S>& p) { return p.a + p.b; }
+template <class S> LCDM_HD S pprod(const CPair<S>& p) { return norm2(p.c); }
+template <class S> LCDM_HD S pprod(const RPair<S>& p) { return p.a * p.b; }
+// exchange the members
+template <class S> LCDM_HD CPair<S> pswap(const CPair<S>& p) { return mkcp(conj(p.c)); }
+template <class S> LCDM_HD RPair<S> pswap(const RPair<S>& p) { return mkrp(p.b, p.a); }
+// member-wise arithmetic
+template <class S> LCDM_HD CPair<S> operator+(const CPair<S>& p, const CPair<S>& q) { return mkcp(p.c + q.c); }
+template <class S> LCDM_HD RPair<S> operator+(const RPair<S>& p, const RPair<S>& q) { return mkrp(p.a + q.a, p.b + q.b); }
+template <class S> LCDM_HD CPair<S> operator-(const CPair<S>& p, const CPair<S>& q) { return mkcp(p.c - q.c); }
+template <class S> LCDM_HD RPair<S> operator-(const RPair<S>& p, const RPair<S>& q) { return mkrp(p.a - q.a, p.b - q.b); }
+template <class S> LCDM_HD CPair<S> operator*(const CPair<S>& p, const CPair<S>& q) { return mkcp(p.c * q.c); }
+template <class S> LCDM_HD RPair<S> operator*(const RPair<S>& p, const RPair<S>& q) { return mkrp(p.a * q.a, p.b * q.b); }
+template <class S> LCDM_HD CPair<S> operator/(const CPair<S>& p, const CPair<S>& q) { return mkcp(p.c / q.c); }
+template <class S> LCDM_HD RPair<S> operator/(const RPair<S>& p, const RPair<S>& q) { return mkrp(p.a / q.a, p.b / q.b); }
+template <class S, class R> LCDM_HD CPair<S> padd(const CPair<S>& p, const R& s) { return mkcp(cxadd(p.c, s)); }
+template <class S, class R> LCDM_HD RPair<S> padd(const RPair<S>& p, const R& s) { return mkrp<S>(p.a + s, p.b + s); }
+template <class S, class R> LCDM_HD CPair<S> prsub(const R& s, const CPair<S>& p) { return mkcp(cxrsub(s, p.c)); }
+template <class S, class R> LCDM_HD RPair<S> prsub(const R& s, const RPair<S>& p) { return mkrp<S>(s - p.a, s - p.b); }
+template <class S, class R> LCDM_HD CPair<S> pscale(const CPair<S>& p, const R& s) { return mkcp(cxscale(p.c, s)); }
+template <class S, class R> LCDM_HD RPair<S> pscale(const RPair<S>& p, const R& s) { return mkrp<S>(p.a * s, p.b * s); }
+template <class S> LCDM_HD CPair<S> psqrt(const CPair<S>& p) { return mkcp(cxsqrt(p.c)); }
+template <class S> LCDM_HD RPair<S> psqrt(const RPair<S>& p) { return mkrp(ssqrt(p.a), ssqrt(p.b)); }
+template <class S> LCDM_HD CPair<S> prcp(const CPair<S>& p) { return mkcp(cxrcp(p.c)); }
+template <class S> LCDM_HD RPair<S> prcp(const RPair<S>& p) {
+    return mkrp<S>(cst_like(p.a, 1.0) / p.a, cst_like(p.b, 1.0) / p.b);
+}
+// sum over members of c_m * x_m (real)
+template <class T> LCDM_HD T pdot(const CPair<T>& c, const CPair<T>& x) {
+    return cst<T>(2.0) * (c.c.re * x.c.re - c.c.im * x.c.im);
+}
+template <class T> LCDM_HD T pdot(const RPair<T>& c, const RPair<T>& x) { return c.a * x.a + c.b * x.b; }
+// sum over members of c_m * (tangent k of x_m)
+template <class T, int K> LCDM_HD T pdot_k(const CPair<T>& c, const CPair<Dual<T, K> >& x, int k) {
+    return cst<T>(2.0) * (c.c.re * x.c.re.d[k] - c.c.im * x.c.im.d[k]);
+}
+template <class T, int K> LCDM_HD T pdot_k(const RPair<T>& c, const RPair<Dual<T, K> >& x, int k) {
+    return c.a * x.a.d[k] + c.b * x.b.d[k];
+}
+// values of a dual pair
+template <class T, int K> LCDM_HD CPair<T> pval(const CPair<Dual<T, K> >& p) { return mkcp(mkcx<T>(p.c.re.v, p.c.im.v)); }
+template <class T, int K> LCDM_HD RPair<T> pval(const RPair<Dual<T, K> >& p) { return mkrp<T>(p.a.v, p.b.v); }
+template <class T> LCDM_HD CPair<T> pval(const CPair<T>& p) { return p; }
+template <class T> LCDM_HD RPair<T> pval(const RPair<T>& p) { return p; }
+// largest squared distance of a member from a real point
+template <class T> LCDM_HD T pdev2(const CPair<T>& p, T mu) {
+    T d = p.c.re - mu; return d * d + p.c.im * p.c.im;
+}
+template <class T> LCDM_HD T pdev2(const RPair<T>& p, T mu) {
+    T da = p.a - mu, db = p.b - mu;
+    T a2 = da * da, b2 = db * db;
+    return sval(a2) > sval(b2) ? a2 : b2;
+}
+// largest member modulus (for scaling)
+template <class T> LCDM_HD float pmag(const CPair<T>& p) {
+    float r = fabsf((float)sval(p.c.re)), i = fabsf((float)sval(p.c.im));
+    return r > i ? r : i;
+}
+template <class T> LCDM_HD float pmag(const RPair<T>& p) {
+    float a = fabsf((float)sval(p.a)), b = fabsf((float)sval(p.b));
+    return a > b ? a : b;
+}
+template <class T> LCDM_HD CPair<T> pldexp(const CPair<T>& p, int e) {
+    return mkcp(mkcx<T>(sldexp(p.c.re, e), sldexp(p.c.im, e)));
+}
+template <class T> LCDM_HD RPair<T> pldexp(const RPair<T>& p, int e) { return mkrp<T>(sldexp(p.a, e), sldexp(p.b, e)); }
+
+// ---------------------------------------------------------------------------
+// Carlson's duplication algorithm (ref. [10]).
+// Deviation tolerance: the iteration stops once every argument is within
+// tol * mean of the common mean; the truncated series is then exact to
+// about tol^6, i.e. below the working precision.
+// ---------------------------------------------------------------------------
+template <class T> struct Prec;
+template <> struct Prec<float> {
+    static LCDM_HD float tol() { return 0.04f; }
+    static LCDM_HD float rc_series_max() { return 0.1f; }
+    enum { rc_terms = 8, maxit = 24 };
+};
+template <> struct Prec<double> {
+    static LCDM_HD double tol() { return 1.5e-3; }
+    static LCDM_HD double rc_series_max() { return 0.03; }
+    enum { rc_terms = 12, maxit = 40 };
+};
+template <> struct Prec<df64> {
+    static LCDM_HD df64 tol() { return mkdf(3e-3f); }
+    static LCDM_HD df64 rc_series_max() { return mkdf(0.03f); }
+    enum { rc_terms = 12, maxit = 40 };
+};
+
+// R_C(x, y) = R_F(x, y, y) (eq. 2.8) by duplication; value only.
+template <class T> LCDM_HD T rc_value(T x, T y, int* fail) {
+    const T tol = Prec<T>::tol();
+    int m = 0;
+    T A = (x + y + y) * cst<T>(1.0 / 3.0);
+    for (; m < Prec<T>::maxit; m++) {
+        T dv = sabs(y - A);
+        if (sval(dv) <= sval(tol * sabs(A))) break;
+        T lam = cst<T>(2.0) * ssqrt(x) * ssqrt(y) + y;
+        x = (x + lam) * cst<T>(0.25);
+        y = (y + lam) * cst<T>(0.25);
+        A = (x + y + y) * cst<T>(1.0 / 3.0);
+    }
+    if (m == Prec<T>::maxit) *fail = 1;
+    T s = (y - A) / A;
+    T ser = cst<T>(159.0 / 208.0) + s * cst<T>(9.0 / 8.0);
+    ser = cst<T>(9.0 / 22.0) + s * ser;
+    ser = cst<T>(3.0 / 8.0) + s * ser;
+    ser = cst<T>(1.0 / 7.0) + s * ser;
+    ser = cst<T>(3.0 / 10.0) + s * ser;
+    ser = cst<T>(1.0) + s * s * ser;
+    return ser / ssqrt(A);
+}
+
+// R_C(1, 1 + e) for |e| < 1: sum_n (-e)^n / (2n+1) when e is small, else duplication.
+template <class T> LCDM_HD T rc1(T e, int* fail) {
+    if (sval(sabs(e)) <= sval(Prec<T>::rc_series_max())) {
+        T w = -e;
+        T s = cst<T>(1.0 / (2 * Prec<T>::rc_terms + 1));
+#pragma unroll
+        for (int n = Prec<T>::rc_terms - 1; n >= 0; n--) s = cst<T>(1.0 / (2 * n + 1)) + w * s;
+        return s;
+    }
+    return rc_value(cst<T>(1.0), cst<T>(1.0) + e, fail);
+}
+
+// Series of R_J (and of R_D = R_J with p equal to one argument) in the
+// normalised deviations: X for the single argument, sumY / prodY for the pair,
+// P for p.  U is a scalar or a complex type.
+template <class U, class T> LCDM_HD U rj_series(U X, U sumY, U prodY, U P) {
+    U XYZ = X * prodY;
+    U P2 = P * P;
+    U E2 = X * sumY + prodY - P2 * cst<T>(3.0);
+    U E3 = XYZ + E2 * P * cst<T>(2.0) + P2 * P * cst<T>(4.0);
+    U E4 = (XYZ * cst<T>(2.0) + E2 * P + P2 * P * cst<T>(3.0)) * P;
+    U E5 = XYZ * P2;
+    return cst<T>(1.0) - E2 * cst<T>(3.0 / 14.0) + E3 * cst<T>(1.0 / 6.0) + E2 * E2 * cst<T>(9.0 / 88.0)
+           - E4 * cst<T>(3.0 / 22.0) - E2 * E3 * cst<T>(9.0 / 52.0) + E5 * cst<T>(3.0 / 26.0);
+}
+// complex x real helpers for the pair-special R_D series
+template <class T> LCDM_HD Cx<T> operator*(const Cx<T>& a, const T& s) { return mkcx<T>(a.re * s, a.im * s); }
+template <class T> LCDM_HD Cx<T> operator+(const Cx<T>& a, const T& s) { return mkcx<T>(a.re + s, a.im); }
+template <class T> LCDM_HD Cx<T> operator-(const T& s, const Cx<T>& a) { return mkcx<T>(s - a.re, -a.im); }
+template <class T> LCDM_HD Cx<T> operator-(const Cx<T>& a, const T& s) { return mkcx<T>(a.re - s, a.im); }
+
+template <class T, int NJ, class PT>
+struct DupResult {
+    T RF;      // R_F(x1, x2, x3)
+    T RD1;     // R_D(x2, x3, x1): x1 special
+    PT RDp;    // R_D(x1, x3, x2), R_D(x1, x2, x3): pair member special
+    T RJ[NJ];  // R_J(x1, x2, x3, p_j)
+};
+
+// R_D with a pair member special, from the final duplicated arguments.
+template <class T> LCDM_HD CPair<T> rd_pair_series(T x1, const CPair<T>& pr, T f, const CPair<T>& sDp) {
+    Cx<T> c = pr.c, cb = conj(pr.c);
+    Cx<T> A = mkcx<T>((x1 + c.re + c.re) * cst<T>(0.2), cst<T>(0.0)) + c * cst<T>(0.4);
+    Cx<T> iA = cxrcp(A);
+    Cx<T> X = (mkcx<T>(cst<T>(0.0), cst<T>(0.0)) + (A - x1)) * iA;
+    Cx<T> Ym = (A - c) * iA, Yo = (A - cb) * iA;
+    Cx<T> ser = rj_series<Cx<T>, T>(X, Ym + Yo, Ym * Yo, Ym);
+    Cx<T> sA = cxsqrt(A);
+    Cx<T> r = ser * f / (A * sA) + sDp.c * cst<T>(3.0);
+    return mkcp(r);
+}
+template <class T> LCDM_HD RPair<T> rd_pair_series(T x1, const RPair<T>& pr, T f, const RPair<T>& sDp) {
+    RPair<T> out;
+    {
+        T A = (x1 + pr.b + cst<T>(3.0) * pr.a) * cst<T>(0.2), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA, Ym = (A - pr.a) * iA, Yo = (A - pr.b) * iA;
+        out.a = f * rj_series<T, T>(X, Ym + Yo, Ym * Yo, Ym) * iA / ssqrt(A) + cst<T>(3.0) * sDp.a;
+    }
+    {
+        T A = (x1 + pr.a + cst<T>(3.0) * pr.b) * cst<T>(0.2), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA, Ym = (A - pr.b) * iA, Yo = (A - pr.a) * iA;
+        out.b = f * rj_series<T, T>(X, Ym + Yo, Ym * Yo, Ym) * iA / ssqrt(A) + cst<T>(3.0) * sDp.b;
+    }
+    return out;
+}
+template <class T> LCDM_HD CPair<T> pzero(const CPair<T>&) { return mkcp(mkcx<T>(cst<T>(0.0), cst<T>(0.0))); }
+template <class T> LCDM_HD RPair<T> pzero(const RPair<T>&) { return mkrp<T>(cst<T>(0.0), cst<T>(0.0)); }
+
+LCDM_HD int even_exponent(float mag) {
+    int e = (mag > 0.f && mag < 3.0e38f) ? ilogbf(mag) : 0;
+    return e & ~1;
+}
+
+// One duplication sequence for R_F, R_D (all three specials when WANT_D) and
+// NJ R_J tracks with p_j > 0.  The triple is (x1, pair).  Arguments are first
+// scaled by an even power of two (exact; R_F ~ s^-1/2, R_D and R_J ~ s^-3/2).
+template <class T, int NJ, bool WANT_D, class PT>
+LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail) {
+    DupResult<T, NJ, PT> R;
+    float mag = fabsf((float)sval(x1));
+    float pm = pmag(pr);
+    if (pm > mag) mag = pm;
+    T p[NJ > 0 ? NJ : 1];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        p[j] = pj[j];
+        float a = fabsf((float)sval(p[j]));
+        if (a > mag) mag = a;
+    }
+    const int e = even_exponent(mag);
+    x1 = sldexp(x1, -e);
+    pr = pldexp(pr, -e);
+    T delta[NJ > 0 ? NJ : 1], sJ[NJ > 0 ? NJ : 1];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        p[j] = sldexp(p[j], -e);
+        delta[j] = (p[j] - x1) * pprod(prsub(p[j], pr));
+        sJ[j] = cst<T>(0.0);
+    }
+    T sD1 = cst<T>(0.0);
+    PT sDp = pzero(pr);
+    T f = cst<T>(1.0);
+    const T tol = Prec<T>::tol();
+    int m = 0;
+    for (; m < Prec<T>::maxit; m++) {
+        T mu = x1 + psum(pr);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) mu = mu + p[j];
+        mu = mu * cst<T>(1.0 / (3 + NJ));
+        T lim = tol * mu;
+        T lim2 = lim * lim;
+        T dx = x1 - mu;
+        bool conv = sval(dx * dx) <= sval(lim2) && sval(pdev2(pr, mu)) <= sval(lim2);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            T dp = p[j] - mu;
+            conv = conv && sval(dp * dp) <= sval(lim2);
+        }
+        if (conv) break;
+        T s1 = ssqrt(x1);
+        PT sp = psqrt(pr);
+        T lam = s1 * psum(sp) + pprod(sp);
+        if (WANT_D) {
+            sD1 = sD1 + f / (s1 * (x1 + lam));
+            sDp = sDp + pscale(prcp(sp * padd(pr, lam)), f);
+        }
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            T sq = ssqrt(p[j]);
+            T d = (sq + s1) * pprod(padd(sp, sq));
+            T f3 = f * f * f;
+            T ee = f3 * delta[j] / (d * d);
+            sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
+        }
+        x1 = (x1 + lam) * cst<T>(0.25);
+        pr = pscale(padd(pr, lam), cst<T>(0.25));
+#pragma unroll
+        for (int j = 0; j < NJ; j++) p[j] = (p[j] + lam) * cst<T>(0.25);
+        f = f * cst<T>(0.25);
+    }
+    if (m == Prec<T>::maxit) *fail = 1;
+    // R_F series
+    {
+        T A = (x1 + psum(pr)) * cst<T>(1.0 / 3.0), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA;
+        PT Y = pscale(prsub(A, pr), iA);
+        T e2 = X * psum(Y) + pprod(Y), e3 = X * pprod(Y);
+        T ser = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
+                - e2 * e3 * cst<T>(3.0 / 44.0);
+        R.RF = sldexp(ser / ssqrt(A), -e / 2);
+    }
+    if (WANT_D) {
+        T A = (psum(pr) + cst<T>(3.0) * x1) * cst<T>(0.2), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA;
+        PT Y = pscale(prsub(A, pr), iA);
+        T ser = rj_series<T, T>(X, psum(Y), pprod(Y), X);
+        R.RD1 = sldexp(f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1, -3 * e / 2);
+        R.RDp = pldexp(rd_pair_series(x1, pr, f, sDp), -3 * e / 2);
+    }
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        T A = (x1 + psum(pr) + cst<T>(2.0) * p[j]) * cst<T>(0.2), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA, P = (A - p[j]) * iA;
+        PT Y = pscale(prsub(A, pr), iA);
+        T ser = rj_series<T, T>(X, psum(Y), pprod(Y), P);
+        R.RJ[j] = sldexp(f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j], -3 * e / 2);
+    }
+    return R;
+}
+
+}  // namespace lcdm

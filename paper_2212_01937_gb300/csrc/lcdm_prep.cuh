@@ -1,0 +1,241 @@
+// Root preparation, one thread per cosmology, FP64: factorise E^2 (eq. 3.2),
+// classify the roots, choose the root labels, precompute the per-cosmology
+// constants and the root tangents (App. A, eqs. A.1-A.4).
+#pragma once
+#include "lcdm_kernels.cuh"
+
+namespace lcdm {
+
+// ---------------------------------------------------------------- roots -----
+struct cd { double re, im; };
+__device__ __forceinline__ cd cmk(double r, double i) { cd c; c.re = r; c.im = i; return c; }
+__device__ __forceinline__ cd cadd(cd a, cd b) { return cmk(a.re + b.re, a.im + b.im); }
+__device__ __forceinline__ cd csub(cd a, cd b) { return cmk(a.re - b.re, a.im - b.im); }
+__device__ __forceinline__ cd cmul(cd a, cd b) { return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+__device__ __forceinline__ cd cdiv(cd a, cd b) {
+    double s = fabs(b.re) > fabs(b.im) ? fabs(b.re) : fabs(b.im);
+    double br = b.re / s, bi = b.im / s, n = br * br + bi * bi;
+    return cmk((a.re * br + a.im * bi) / (s * n), (a.im * br - a.re * bi) / (s * n));
+}
+__device__ __forceinline__ double cabs_(cd a) { return hypot(a.re, a.im); }
+__device__ __forceinline__ cd csqrt_(cd a) {
+    double r = cabs_(a);
+    if (a.re >= 0) { double t = sqrt(0.5 * (r + a.re)); return cmk(t, t > 0 ? a.im / (2 * t) : 0.0); }
+    double t = sqrt(0.5 * (r - a.re));
+    return cmk(fabs(a.im) / (2 * t), a.im < 0 ? -t : t);
+}
+
+// p(x) = sum_k c[k] x^k (degree n, c[n] = 1) and p'(x) by Horner's rule
+__device__ __forceinline__ void horner(const double* c, int n, cd x, cd& p, cd& dp) {
+    p = cmk(c[n], 0); dp = cmk(0, 0);
+    for (int k = n - 1; k >= 0; k--) { dp = cadd(cmul(dp, x), p); p = cadd(cmul(p, x), cmk(c[k], 0)); }
+}
+
+// Roots of the monic polynomial c (degree n <= 4) by the Aberth-Ehrlich
+// iteration started on circles whose radii come from the Newton polygon of
+// log|c_k| (so a root near -Om/Or and the O(1) roots both start close).
+__device__ int poly_roots(const double* c, int n, cd* z) {
+    // upper convex hull of (k, log|c_k|)
+    double lg[5];
+    int idx[5], m = 0;
+    for (int k = 0; k <= n; k++) lg[k] = c[k] != 0 ? log(fabs(c[k])) : -1e300;
+    for (int k = 0; k <= n; k++) {
+        if (c[k] == 0) continue;
+        while (m >= 2) {
+            int a = idx[m - 2], b = idx[m - 1];
+            // remove b if it lies below the segment a-k
+            if ((lg[b] - lg[a]) * (k - a) <= (lg[k] - lg[a]) * (b - a)) m--; else break;
+        }
+        idx[m++] = k;
+    }
+    int r = 0;
+    for (int e = 0; e + 1 < m; e++) {
+        int a = idx[e], b = idx[e + 1], w = b - a;
+        double rad = exp((lg[a] - lg[b]) / w);
+        for (int j = 0; j < w; j++) {
+            double ang = 2.0 * CUDART_PI * j / w + 2.0 * CUDART_PI * a / n + 0.4;
+            z[r++] = cmk(rad * cos(ang), rad * sin(ang));
+        }
+    }
+    for (; r < n; r++) z[r] = cmk(0.5 * r + 0.1, 0.3);  // (zero constant term etc.)
+    int it = 0, settled = 0;
+    for (; it < 200; it++) {
+        double maxrel = 0;
+        for (int i = 0; i < n; i++) {
+            cd p, dp;
+            horner(c, n, z[i], p, dp);
+            if (p.re == 0 && p.im == 0) continue;
+            cd ratio = cdiv(p, dp);
+            cd s = cmk(0, 0);
+            for (int j = 0; j < n; j++)
+                if (j != i) s = cadd(s, cdiv(cmk(1, 0), csub(z[i], z[j])));
+            cd w = cdiv(ratio, csub(cmk(1, 0), cmul(ratio, s)));
+            z[i] = csub(z[i], w);
+            double rel = cabs_(w) / (cabs_(z[i]) + 1e-300);
+            if (rel > maxrel) maxrel = rel;
+        }
+        if (maxrel < 1e-15) { if (++settled >= 2) break; }
+    }
+    // Newton polishing
+    for (int i = 0; i < n; i++) {
+        for (int k = 0; k < 2; k++) {
+            cd p, dp;
+            horner(c, n, z[i], p, dp);
+            if (dp.re == 0 && dp.im == 0) break;
+            cd zn = csub(z[i], cdiv(p, dp)), pn, dpn;
+            horner(c, n, zn, pn, dpn);
+            if (cabs_(pn) <= cabs_(p)) z[i] = zn; else break;
+        }
+    }
+    return it;
+}
+
+__device__ __forceinline__ void polish_real(const double* c, int n, double& x) {
+    for (int k = 0; k < 3; k++) {
+        double p = c[n], dp = 0;
+        for (int j = n - 1; j >= 0; j--) { dp = dp * x + p; p = p * x + c[j]; }
+        if (dp == 0) return;
+        double xn = x - p / dp, pn = c[n];
+        for (int j = n - 1; j >= 0; j--) pn = pn * xn + c[j];
+        if (fabs(pn) <= fabs(p)) x = xn; else return;
+    }
+}
+
+// One thread per cosmology.  params [B][ncol] = (H0, Om, OL, Or[, Ok]).
+// grad / loglike (optional): rows initialised to 0 (NaN for a bad status).
+__global__ void prep_kernel(const double* __restrict__ params, int64_t B, int ncol, double* __restrict__ recD,
+                            float2* __restrict__ recF, int32_t* __restrict__ status, double* __restrict__ grad,
+                            double* __restrict__ loglike) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    const double* p = params + b * ncol;
+    double H0 = p[0], Om = p[1], OL = p[2], Or = p[3];
+    double Ok = ncol >= 5 ? p[4] : 1.0 - Om - OL - Or;
+    double rec[NREC];
+    for (int i = 0; i < NREC; i++) rec[i] = 0;
+    int st = ST_OK, kind = 0;
+    const int K = ncol - 1;
+    bool finite = isfinite(H0) && isfinite(Om) && isfinite(OL) && isfinite(Or) && isfinite(Ok);
+    int n = Or > 0 ? 4 : 3;
+    if (!finite || !(H0 > 0) || Or < 0 || (n == 3 && !(Om > 0))) st = ST_INVALID;
+    cd z[4];
+    double alpha[5] = {OL, 0.0, Ok, Om, Or};
+    double an = alpha[n];
+    double c[5];
+    if (st == ST_OK) {
+        for (int k = 0; k <= n; k++) c[k] = alpha[k] / an;
+        c[n] = 1.0;
+        poly_roots(c, n, z);
+        // classification: real when the imaginary part is negligible
+        int nreal = 0, ir[4], ic[4], ncx = 0;
+        for (int i = 0; i < n; i++) {
+            if (fabs(z[i].im) <= 1e-12 * cabs_(z[i])) { z[i].im = 0; polish_real(c, n, z[i].re); ir[nreal++] = i; }
+            else ic[ncx++] = i;
+        }
+        for (int i = 0; i < nreal; i++)
+            if (z[ir[i]].re >= 1.0) st = ST_NO_BIG_BANG;   // real root at z >= 0 (Sec. 3, Fig. 1)
+        // order reals by decreasing |rho| (fn15: largest roots of E^2(z+1))
+        for (int i = 0; i < nreal; i++)
+            for (int j = i + 1; j < nreal; j++)
+                if (fabs(z[ir[j]].re) > fabs(z[ir[i]].re)) { int t = ir[i]; ir[i] = ir[j]; ir[j] = t; }
+        cd A, Bv, P1, P2;
+        bool cpair = false;
+        if (n == 4 && nreal == 2 && ncx == 2) {
+            kind = 0; A = z[ir[0]]; Bv = z[ir[1]]; cpair = true;
+            P1 = z[ic[0]].im > 0 ? z[ic[0]] : z[ic[1]];
+            P1.im = 0.5 * (fabs(z[ic[0]].im) + fabs(z[ic[1]].im));
+            P1.re = 0.5 * (z[ic[0]].re + z[ic[1]].re);
+        } else if (n == 4 && nreal == 4) {
+            kind = 1; A = z[ir[0]]; Bv = z[ir[1]]; P1 = z[ir[2]]; P2 = z[ir[3]];
+        } else if (n == 3 && nreal == 1 && ncx == 2) {
+            kind = 2; A = z[ir[0]]; Bv = cmk(0, 0); cpair = true;
+            P1 = z[ic[0]].im > 0 ? z[ic[0]] : z[ic[1]];
+            P1.im = 0.5 * (fabs(z[ic[0]].im) + fabs(z[ic[1]].im));
+            P1.re = 0.5 * (z[ic[0]].re + z[ic[1]].re);
+        } else if (n == 3 && nreal == 3) {
+            kind = 3; A = z[ir[0]]; Bv = cmk(0, 0); P1 = z[ir[1]]; P2 = z[ir[2]];
+        } else if (st == ST_OK) {
+            st = ST_UNSUPPORTED;   // e.g. two complex pairs (no real root)
+        }
+        if (st == ST_OK || st == ST_NO_BIG_BANG) {
+            // roots in x = 1+z for the derivatives; stored in z
+            cd rho[4];
+            int nr = 0;
+            rho[nr++] = A;
+            if (n == 4) rho[nr++] = Bv;
+            rho[nr++] = P1;
+            rho[nr++] = cpair ? cmk(P1.re, -P1.im) : P2;
+            if (A.re == 0.0) st = st == ST_OK ? ST_DEGENERATE : st;   // division by rho_A in eq. (3.8)
+            rec[RF_A] = A.re - 1.0;
+            rec[RF_B] = (n == 4 ? Bv.re : 1.0) - 1.0;
+            if (cpair) { rec[RF_PRE] = P1.re - 1.0; rec[RF_PIM] = P1.im; }
+            else { rec[RF_PRE] = P1.re - 1.0; rec[RF_PIM] = P2.re - 1.0; }
+            rec[RF_YA] = sqrt(-rec[RF_A]);
+            rec[RF_YB] = sqrt(-rec[RF_B]);
+            if (cpair) { cd y = csqrt_(cmk(-rec[RF_PRE], -rec[RF_PIM])); rec[RF_YPRE] = y.re; rec[RF_YPIM] = y.im; }
+            else { rec[RF_YPRE] = sqrt(-rec[RF_PRE]); rec[RF_YPIM] = sqrt(-rec[RF_PIM]); }
+            // App. A: d rho_j / d c_i = -rho_j^i / prod_{m != j} (rho_j - rho_m)  (eqs. A.2-A.4)
+            cd dr[4][4];
+            for (int j = 0; j < nr; j++) {
+                cd den = cmk(1, 0);
+                for (int m2 = 0; m2 < nr; m2++)
+                    if (m2 != j) den = cmul(den, csub(rho[j], rho[m2]));
+                if (den.re == 0 && den.im == 0) st = (st == ST_OK) ? ST_DEGENERATE : st;
+                for (int k = 0; k < K; k++) {
+                    // d alpha / d theta_k; theta = (Om, OL, Or[, Ok]); closure couples Ok
+                    double da[5] = {0, 0, 0, 0, 0};
+                    if (k == 0) da[3] = 1;
+                    if (k == 1) da[0] = 1;
+                    if (k == 2) da[4] = 1;
+                    if (k == 3) da[2] = 1;
+                    if (ncol == 4) da[2] -= 1;
+                    cd s = cmk(0, 0), pw = cmk(1, 0);
+                    for (int i = 0; i < n; i++) {
+                        double dci = (da[i] * an - alpha[i] * da[n]) / (an * an);
+                        s = cadd(s, cmul(pw, cmk(dci, 0)));
+                        pw = cmul(pw, rho[j]);
+                    }
+                    dr[j][k] = cmk(0, 0);
+                    if (den.re != 0 || den.im != 0) dr[j][k] = cdiv(cmk(-s.re, -s.im), den);
+                    if (n == 3 && k == 2) dr[j][k] = cmk(CUDART_NAN, CUDART_NAN);  // no Or direction in a cubic
+                }
+            }
+            for (int k = 0; k < K; k++) {
+                rec[RF_DA + k] = dr[0][k].re;
+                rec[RF_DB + k] = n == 4 ? dr[1][k].re : 0.0;
+                int jp = n == 4 ? 2 : 1;
+                if (cpair) { rec[RF_DPRE + k] = dr[jp][k].re; rec[RF_DPIM + k] = dr[jp][k].im; }
+                else { rec[RF_DPRE + k] = dr[jp][k].re; rec[RF_DPIM + k] = dr[jp + 1][k].re; }
+            }
+        }
+    }
+    // prefactors: alpha_m^-1/2 (Or for the quartic, Om for the cubic, eq. 3.2 / fn13)
+    double amh = 1.0 / sqrt(n == 4 ? Or : Om);
+    rec[RF_AMH] = amh;
+    rec[RF_OK] = Ok;
+    rec[RF_H0] = H0;
+    rec[RF_DH] = LCDM_C_KMS / H0;
+    rec[RF_TH] = LCDM_HUBBLE_GYR / H0;
+    rec[RF_KIND] = kind;
+    for (int k = 0; k < K; k++) {
+        rec[RF_DAMH + k] = 0;
+        if (n == 4 && k == 2) rec[RF_DAMH + k] = -0.5 * amh / Or;
+        if (n == 3 && k == 0) rec[RF_DAMH + k] = -0.5 * amh / Om;
+        if (n == 3 && k == 2) rec[RF_DAMH + k] = CUDART_NAN;
+        rec[RF_DOK + k] = ncol == 4 ? -1.0 : (k == 3 ? 1.0 : 0.0);
+    }
+    double* rd = recD + b * NREC;
+    float2* rf = recF + b * NREC;
+    for (int i = 0; i < NREC; i++) {
+        rd[i] = rec[i];
+        float h = (float)rec[i];
+        rf[i] = make_float2(h, (float)(rec[i] - (double)h));
+    }
+    status[b] = st;
+    double init = st == ST_OK ? 0.0 : CUDART_NAN;
+    if (grad)
+        for (int k = 0; k < ncol; k++) grad[b * ncol + k] = init;
+    if (loglike) loglike[b] = init;
+}
+
+}  // namespace lcdm

@@ -1,0 +1,248 @@
+"""Thin Python binding of liblcdm (include/lcdm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of liblcdm.so.  PyTorch provides device memory and the stream.  There
+is no fallback: if the library is missing, :func:`load` raises.
+
+Layouts (see include/lcdm.h): ``"csr"`` (offsets [B+1] int64, z [nnz]),
+``"dense"`` (z [B*n], n per row) and ``"shared"`` (z [n] shared by all rows).
+Precision ``"fp32"`` (LCDM_FP32_MIXED: float32 I/O, FP64 roots and
+reductions, double-float island for X and the tangent of t) or ``"fp64"``.
+"""
+import ctypes
+import os
+
+import torch
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "liblcdm.so")
+OUTS = ("d_C", "t", "X", "d_M", "d_L", "mu")
+PRECISION = {"fp64": 0, "fp32": 1}
+LAYOUT = {"csr": 0, "dense": 1, "shared": 2}
+
+_lib = None
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("ncol", ctypes.c_int32), ("precision", ctypes.c_int32), ("layout", ctypes.c_int32),
+                ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+
+
+_vp = ctypes.c_void_p
+_VP6 = ctypes.c_void_p * 6
+
+
+def load():
+    """Load liblcdm.so (built in-tree by build.py); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("liblcdm.so not found at %s; build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`" % LIB_PATH)
+    lib = ctypes.CDLL(LIB_PATH)
+    i64, i32, sz, dbl = ctypes.c_int64, ctypes.c_int32, ctypes.c_size_t, ctypes.c_double
+    op = ctypes.POINTER(Opts)
+    lib.lcdm_workspace_size.argtypes = [i64, op, ctypes.POINTER(sz)]
+    lib.lcdm_roots.argtypes = [_vp, i64, op, _vp, _vp, _vp, _vp, _vp, sz, _vp]
+    lib.lcdm_distances.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _vp, op, _vp, sz, _vp]
+    lib.lcdm_distances_jac.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, op, _vp, sz, _vp]
+    lib.lcdm_distances_vjp.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp]
+    lib.lcdm_gauss_loglike.argtypes = [_vp, i64, _vp, _vp, _vp, i64, dbl, dbl, _vp, _vp, _vp, _vp, op, _vp,
+                                       sz, _vp]
+    lib.lcdm_autotune.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp,
+                                  ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+    lib.lcdm_status_string.argtypes = [ctypes.c_int]
+    lib.lcdm_status_string.restype = ctypes.c_char_p
+    lib.lcdm_launch_count.restype = i64
+    for f in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
+              "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+def _check(st):
+    if st != 0:
+        raise RuntimeError("liblcdm: " + load().lcdm_status_string(st).decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def launch_count():
+    return int(load().lcdm_launch_count())
+
+
+class Call:
+    """Prepared arguments of one batch (validated and placed on the device)."""
+
+    def __init__(self, params, z, offsets=None, layout=None, precision="fp32", block=0, blocks_per_sm=0,
+                 workspace=None):
+        lib = load()
+        if not params.is_cuda:
+            raise ValueError("params must be a CUDA tensor")
+        self.device = params.device
+        self.params = params.to(torch.float64).contiguous()
+        self.B, ncol = self.params.shape
+        if layout is None:
+            layout = "csr" if offsets is not None else "dense"
+        self.layout = layout
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.z = z.to(device=self.device, dtype=self.dtype).contiguous().reshape(-1)
+        self.offsets = None
+        if layout == "csr":
+            if offsets is None:
+                raise ValueError("csr layout needs offsets")
+            self.offsets = offsets.to(device=self.device, dtype=torch.int64).contiguous()
+            self.n = self.z.numel()
+            self.npairs = self.n
+        elif layout == "dense":
+            if self.z.numel() % self.B:
+                raise ValueError("dense layout needs len(z) divisible by B")
+            self.n = self.z.numel() // self.B
+            self.npairs = self.z.numel()
+        else:
+            self.n = self.z.numel()
+            self.npairs = self.B * self.n
+        self.opts = Opts(ncol, PRECISION[precision], LAYOUT[layout], block, blocks_per_sm)
+        nbytes = ctypes.c_size_t()
+        _check(lib.lcdm_workspace_size(self.B, ctypes.byref(self.opts), ctypes.byref(nbytes)))
+        if workspace is not None and workspace.numel() >= nbytes.value:
+            self.ws = workspace
+        else:
+            self.ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self.ws_bytes = self.ws.numel()
+        self.status = torch.empty(self.B, dtype=torch.int32, device=self.device)
+
+    @property
+    def ncol(self):
+        return self.opts.ncol
+
+    def out_buffers(self, outputs):
+        out = {}
+        for name in outputs:
+            if name not in OUTS:
+                raise ValueError("unknown output %r" % name)
+            out[name] = torch.empty(self.npairs, dtype=self.dtype, device=self.device)
+        return out, _VP6(*[(out[n].data_ptr() if n in out else None) for n in OUTS])
+
+    def common(self):
+        return (_ptr(self.params), self.B, _ptr(self.offsets), _ptr(self.z), self.n)
+
+    def tail(self):
+        return (ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes, _stream(self.device))
+
+
+def roots(params):
+    """Roots of E^2 in z with their derivatives (lcdm_roots)."""
+    c = Call(params, torch.zeros(params.shape[0], device=params.device), layout="dense", precision="fp64")
+    r = torch.empty(c.B, 4, 2, dtype=torch.float64, device=c.device)
+    dr = torch.empty(c.B, 4, 2, c.ncol - 1, dtype=torch.float64, device=c.device)
+    kind = torch.empty(c.B, dtype=torch.int32, device=c.device)
+    _check(load().lcdm_roots(_ptr(c.params), c.B, ctypes.byref(c.opts), _ptr(r), _ptr(dr), _ptr(kind),
+                             _ptr(c.status), _ptr(c.ws), c.ws_bytes, _stream(c.device)))
+    return {"roots": torch.complex(r[..., 0], r[..., 1]), "droots": torch.complex(dr[..., 0, :], dr[..., 1, :]),
+            "kind": kind, "status": c.status}
+
+
+def distances(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), **kw):
+    """Forward distances (lcdm_distances).  Returns {name: tensor, "status": ...}."""
+    c = Call(params, z, offsets, **kw)
+    out, vp = c.out_buffers(outputs)
+    _check(load().lcdm_distances(*c.common(), vp, _ptr(c.status), *c.tail()))
+    out["status"] = c.status
+    return out
+
+
+def distances_jac(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), jac_outputs=None, **kw):
+    """Forward distances and per-pair Jacobians [npairs, ncol] (lcdm_distances_jac)."""
+    c = Call(params, z, offsets, **kw)
+    out, vp = c.out_buffers(outputs)
+    jac_outputs = outputs if jac_outputs is None else jac_outputs
+    jac = {n: torch.empty(c.npairs, c.ncol, dtype=c.dtype, device=c.device) for n in jac_outputs}
+    jp = _VP6(*[(jac[n].data_ptr() if n in jac else None) for n in OUTS])
+    _check(load().lcdm_distances_jac(*c.common(), vp, jp, _ptr(c.status), *c.tail()))
+    out["jac"] = jac
+    out["status"] = c.status
+    return out
+
+
+def distances_vjp(params, z, cot, offsets=None, outputs=(), **kw):
+    """Fused forward + adjoint (lcdm_distances_vjp): grad [B, ncol] of
+    sum_o <cot[o], out_o>.  cot: {name: tensor [npairs]}."""
+    c = Call(params, z, offsets, **kw)
+    out, vp = c.out_buffers(outputs)
+    cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items() if v is not None}
+    cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])
+    grad = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device)
+    _check(load().lcdm_distances_vjp(*c.common(), cp, vp, _ptr(grad), _ptr(c.status), *c.tail()))
+    out["grad"] = grad
+    out["status"] = c.status
+    return out
+
+
+def gauss_loglike(params, z, m_obs, offsets=None, M=-19.3, sigma=0.1, grad=True, want_mu=False,
+                  call=None, **kw):
+    """Gaussian log-likelihood of magnitudes per cosmology and its gradient
+    (lcdm_gauss_loglike).  Returns {"loglike": [B], "grad": [B, ncol], ...}."""
+    c = call if call is not None else Call(params, z, offsets, **kw)
+    m = m_obs.to(device=c.device, dtype=c.dtype).contiguous()
+    ll = torch.empty(c.B, dtype=torch.float64, device=c.device)
+    g = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device) if grad else None
+    mu = torch.empty(c.npairs, dtype=c.dtype, device=c.device) if want_mu else None
+    _check(load().lcdm_gauss_loglike(*c.common()[:4], _ptr(m), c.n, float(M), float(sigma), _ptr(ll), _ptr(g),
+                                     _ptr(mu), _ptr(c.status), *c.tail()))
+    res = {"loglike": ll, "status": c.status}
+    if grad:
+        res["grad"] = g
+    if want_mu:
+        res["mu"] = mu
+    return res
+
+
+def autotune(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), cot=None, **kw):
+    """Pick the fastest launch shape for this workload class (lcdm_autotune)."""
+    c = Call(params, z, offsets, **kw)
+    out, vp = c.out_buffers(outputs)
+    cp, grad = None, None
+    if cot is not None:
+        cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items()}
+        cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])
+        grad = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device)
+    bb, bbps, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    _check(load().lcdm_autotune(*c.common(), cp, vp, _ptr(grad), _ptr(c.status), *c.tail(), ctypes.byref(bb),
+                                ctypes.byref(bbps), ctypes.byref(ms)))
+    return {"block": bb.value, "blocks_per_sm": bbps.value, "ms": ms.value}
+
+
+class Distances(torch.autograd.Function):
+    """d_C, t, X, d_M, d_L, mu as differentiable functions of params.
+
+    Forward runs lcdm_distances; backward runs the fused forward+adjoint
+    kernel (lcdm_distances_vjp) with the incoming gradients as cotangents."""
+
+    @staticmethod
+    def forward(ctx, params, z, offsets, outputs, layout, precision):
+        res = distances(params, z, offsets, outputs=outputs, layout=layout, precision=precision)
+        ctx.save_for_backward(params, z, offsets if offsets is not None else torch.empty(0))
+        ctx.meta = (outputs, layout, precision, offsets is not None)
+        return tuple(res[n] for n in outputs)
+
+    @staticmethod
+    def backward(ctx, *grads):
+        params, z, offsets = ctx.saved_tensors
+        outputs, layout, precision, has_off = ctx.meta
+        cot = {n: g for n, g in zip(outputs, grads) if g is not None}
+        res = distances_vjp(params, z, cot, offsets if has_off else None, layout=layout, precision=precision)
+        return res["grad"].to(params.dtype), None, None, None, None, None
+
+
+def distances_autograd(params, z, offsets=None, outputs=("d_C", "mu"), layout=None, precision="fp32"):
+    """Differentiable wrapper: returns a tuple of output tensors."""
+    return Distances.apply(params, z, offsets, tuple(outputs), layout, precision)

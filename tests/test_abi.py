@@ -1,0 +1,64 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and
+exports every entry point include/lcdm.h declares; argument checks that run
+before any CUDA call return the documented status codes."""
+import ctypes
+import os
+import re
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "lcdm.h")
+
+
+def declared_symbols():
+    src = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:lcdm_status|const char\*|int64_t)\s+(lcdm_\w+)\s*\(", src, re.M)))
+
+
+@pytest.fixture(scope="module")
+def cdll():
+    if not shutil.which("nvcc") and not os.path.exists("/usr/local/cuda/bin/nvcc"):
+        pytest.skip("nvcc not available")
+    from paper_2212_01937_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    syms = declared_symbols()
+    for s in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
+              "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_status_string",
+              "lcdm_launch_count"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol(cdll):
+    for s in declared_symbols():
+        assert hasattr(cdll, s), s
+
+
+def test_host_argument_checks(cdll):
+    from paper_2212_01937_gb300.lcdm import Opts
+    cdll.lcdm_status_string.restype = ctypes.c_char_p
+    assert b"OK" in cdll.lcdm_status_string(0)
+    good = Opts(4, 1, 0, 0, 0)
+    n = ctypes.c_size_t()
+    assert cdll.lcdm_workspace_size(ctypes.c_int64(4096), ctypes.byref(good), ctypes.byref(n)) == 0
+    assert n.value >= 4096 * 38 * 16
+    bad = Opts(3, 1, 0, 0, 0)
+    assert cdll.lcdm_workspace_size(ctypes.c_int64(10), ctypes.byref(bad), ctypes.byref(n)) == 1
+    # null params -> invalid before any CUDA call
+    out = (ctypes.c_void_p * 6)()
+    st = cdll.lcdm_distances(None, ctypes.c_int64(1), None, None, ctypes.c_int64(0), out, None,
+                             ctypes.byref(good), None, ctypes.c_size_t(0), None)
+    assert st == 1
+
+
+def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
+    from paper_2212_01937_gb300 import lcdm
+    monkeypatch.setattr(lcdm, "_lib", None)
+    monkeypatch.setattr(lcdm, "LIB_PATH", str(tmp_path / "missing.so"))
+    with pytest.raises(RuntimeError):
+        lcdm.load()

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances (relative unless stated):
+  FP64 path: d_C, t, d_M, d_L <= 1e-12; X <= 1e-10 (eq. 3.9 itself loses
+  digits in double precision); mu <= 1e-11 mag.
+  FP32 path: d_C, t, X, d_M, d_L <= 2e-6; mu <= 1e-5 mag.
+  Gradients: FP64 <= 1e-8 against the Leibniz-rule oracle (itself pinned to
+  central differences at 1e-6); FP32 mu / d_C gradients <= 2e-5.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2212_01937_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+COLS = {"d_C": 0, "t": 1, "X": 2, "d_M": 3, "d_L": 4, "mu": 5}
+TOL64 = {"d_C": 1e-12, "t": 1e-12, "X": 1e-10, "d_M": 1e-12, "d_L": 1e-12}
+TOL32 = {"d_C": 2e-6, "t": 2e-6, "X": 2e-6, "d_M": 2e-6, "d_L": 2e-6}
+
+
+def _t(a, dtype=None):
+    return torch.tensor(np.asarray(a), device=DEV, dtype=dtype)
+
+
+def _batch_small():
+    """Several tiles per row and a ragged tail: 24 rows of varying length."""
+    b = workloads.config2(B=24, n=1, seed=11)
+    rng = np.random.default_rng(11)
+    lens = rng.integers(1, 300, b.B)
+    lens[3] = 0
+    lens[7] = 1
+    offs = np.zeros(b.B + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lens)
+    z = rng.uniform(0.0, 10.0, offs[-1])
+    z[::97] = 0.0
+    z[5::53] = rng.uniform(1e-4, 1e-2, z[5::53].size)
+    z[9::61] = 1100.0
+    return b.params, z, offs
+
+
+def _check(res, ref, tol, prec, names=("d_C", "t", "X", "d_M", "d_L")):
+    for n in names:
+        if n not in res:
+            continue
+        got = res[n].double().cpu().numpy()
+        want = ref[:, COLS[n]]
+        nz = want != 0
+        assert np.all(got[~nz] == 0), n
+        err = np.abs(got[nz] / want[nz] - 1)
+        assert err.max() <= tol[n], (prec, n, err.max(), np.argmax(err))
+    if "mu" in res:
+        got = res["mu"].double().cpu().numpy()
+        want = ref[:, 5]
+        fin = np.isfinite(want)
+        assert np.all(got[~fin] == -np.inf)
+        lim = 1e-11 if prec == "fp64" else 1e-5
+        assert np.max(np.abs(got[fin] - want[fin])) <= lim, (prec, "mu")
+
+
+def test_roots_match_oracle(lib):
+    P = np.vstack([workloads.config2(B=30, n=1, seed=4).params,
+                   [[70, 0.3, 0.7, 0.0], [70, 0.3, 0.7, 1e-5], [60, 0.05, 0.2, 0.0], [70, 0.2, 0.06, 2.4e-5]]])
+    r = lib.roots(_t(P))
+    torch.cuda.synchronize()
+    assert int(r["status"].abs().sum()) == 0
+    got = r["roots"].cpu().numpy() + 1.0          # in x = 1+z, like the oracle
+    rho, nroot = oracle.roots_x(P)
+    J = oracle.root_param_jacobian(P, rho, nroot)
+    dgot = r["droots"].cpu().numpy()
+    kind = r["kind"].cpu().numpy()
+    for b in range(P.shape[0]):
+        m = nroot[b]
+        slots = [0, 1, 2, 3] if m == 4 else [0, 2, 3]
+        assert kind[b] in ((0, 1) if m == 4 else (2, 3))
+        for s in slots:
+            j = np.argmin(np.abs(rho[b, :m] - got[b, s]))
+            assert abs(rho[b, j] - got[b, s]) <= 1e-13 * max(1.0, abs(rho[b, j])), (b, s)
+            for k in range(3):
+                if m == 3 and k == 2:
+                    assert np.isnan(dgot[b, s, k].real)
+                    continue
+                want = J[b, j, k]
+                assert abs(dgot[b, s, k] - want) <= 1e-8 * max(abs(want), 1.0), (b, s, k)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_forward_csr_vs_quadrature(lib, prec):
+    params, z, offs = _batch_small()
+    zin = z if prec == "fp64" else z.astype(np.float32)
+    ref = oracle.quad_distances(params, zin.astype(np.float64), offs)
+    res = lib.distances(_t(params), _t(zin), _t(offs), outputs=("d_C", "t", "X", "d_M", "d_L", "mu"),
+                        precision=prec)
+    torch.cuda.synchronize()
+    assert int(res["status"].abs().sum()) == 0
+    _check(res, ref, TOL64 if prec == "fp64" else TOL32, prec)
+
+
+def test_config1_flat_radiationless(lib):
+    b = workloads.config1()
+    ref = oracle.quad_distances(b.params, b.z, b.offsets)
+    res = lib.distances(_t(b.params), _t(b.z), _t(b.offsets), outputs=("d_C", "mu"), precision="fp64")
+    torch.cuda.synchronize()
+    _check(res, ref, TOL64, "fp64")
+
+
+def test_layouts_agree(lib):
+    b = workloads.config2(B=9, n=70, seed=8)
+    p = _t(b.params)
+    z = _t(b.z.astype(np.float32))
+    dense = lib.distances(p, z, None, layout="dense", outputs=("d_C", "mu"))
+    csr = lib.distances(p, z, _t(b.offsets), layout="csr", outputs=("d_C", "mu"))
+    zs = z[:70]
+    shared = lib.distances(p, zs, None, layout="shared", outputs=("d_C", "mu"))
+    rep = lib.distances(p, zs.repeat(9), None, layout="dense", outputs=("d_C", "mu"))
+    torch.cuda.synchronize()
+    assert torch.equal(dense["d_C"], csr["d_C"]) and torch.equal(dense["mu"], csr["mu"])
+    assert torch.equal(shared["d_C"], rep["d_C"])
+
+
+def test_stress_near_flat_and_near_boundary(lib):
+    s = workloads.config5(B=8, n=40, seed=4)
+    ref = oracle.quad_distances(s.params, s.z, s.offsets)
+    r64 = lib.distances(_t(s.params), _t(s.z), _t(s.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp64")
+    z32 = s.z.astype(np.float32)
+    ref32 = oracle.quad_distances(s.params, z32.astype(np.float64), s.offsets)
+    r32 = lib.distances(_t(s.params), _t(z32), _t(s.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp32")
+    torch.cuda.synchronize()
+    assert int(r64["status"].abs().sum()) == 0
+    # near-coincident roots at the no-Big-Bang boundary limit the root accuracy
+    # to about sqrt(eps): stated looser bounds for this stress set
+    _check(r64, ref, {"d_C": 1e-9, "t": 1e-9, "X": 1e-8}, "fp64", names=("d_C", "t", "X"))
+    _check(r32, ref32, {"d_C": 2e-6, "t": 5e-6, "X": 5e-6}, "fp32", names=("d_C", "t", "X"))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_jacobian_vs_leibniz_oracle(lib, prec):
+    b = workloads.config2(B=6, n=33, seed=9)
+    zin = b.z if prec == "fp64" else b.z.astype(np.float32)
+    _, J = oracle.quad_distances(b.params, zin.astype(np.float64), b.offsets, grad=True)
+    res = lib.distances_jac(_t(b.params), _t(zin), _t(b.offsets), outputs=("d_C", "t", "X", "mu"),
+                            precision=prec)
+    torch.cuda.synchronize()
+    tol = {"fp64": {"d_C": 1e-8, "t": 1e-8, "X": 1e-7, "mu": 1e-8},
+           "fp32": {"d_C": 2e-5, "t": 1e-4, "X": 1e-4, "mu": 2e-5}}[prec]
+    for n, t in tol.items():
+        got = res["jac"][n].double().cpu().numpy()
+        want = J[:, COLS[n], :]
+        scale = np.abs(want).max(axis=1, keepdims=True)
+        err = np.abs(got - want) / scale
+        assert err.max() <= t, (prec, n, err.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_vjp_matches_jacobian_and_oracle(lib, prec):
+    b = workloads.config2(B=7, n=45, seed=10)
+    dt = np.float64 if prec == "fp64" else np.float32
+    rng = np.random.default_rng(1)
+    cot = {n: rng.normal(size=b.nnz).astype(dt) for n in ("d_C", "t", "X", "mu")}
+    zin = b.z.astype(dt)
+    _, J = oracle.quad_distances(b.params, zin.astype(np.float64), b.offsets, grad=True)
+    want = np.zeros((b.B, 4))
+    for r in range(b.B):
+        sl = slice(b.offsets[r], b.offsets[r + 1])
+        for n, c in cot.items():
+            want[r] += (c[sl].astype(np.float64)[:, None] * J[sl, COLS[n], :]).sum(axis=0)
+    res = lib.distances_vjp(_t(b.params), _t(zin), {n: _t(v) for n, v in cot.items()}, _t(b.offsets),
+                            precision=prec)
+    torch.cuda.synchronize()
+    got = res["grad"].cpu().numpy()
+    scale = np.abs(want).max(axis=1, keepdims=True)
+    assert np.max(np.abs(got - want) / scale) <= (1e-8 if prec == "fp64" else 1e-4)
+
+
+def test_gauss_loglike_vs_oracle(lib):
+    b = workloads.config4(B=20, seed=3, nmax_exp=2.5)
+    for prec in ("fp64", "fp32"):
+        dt = np.float64 if prec == "fp64" else np.float32
+        zin, m = b.z.astype(dt), b.m_obs.astype(dt)
+        ref, J = oracle.quad_distances(b.params, zin.astype(np.float64), b.offsets, grad=True)
+        r = (m.astype(np.float64) - ref[:, 5] - b.M) / b.sigma
+        ll = -0.5 * r ** 2 - np.log(b.sigma * np.sqrt(2 * np.pi))
+        want = np.add.reduceat(ll, b.offsets[:-1]) if b.nnz else ll
+        wg = (r / b.sigma)[:, None] * J[:, 5, :]
+        wantg = np.add.reduceat(wg, b.offsets[:-1], axis=0)
+        res = lib.gauss_loglike(_t(b.params), _t(zin), _t(m), _t(b.offsets), M=b.M, sigma=b.sigma, precision=prec)
+        torch.cuda.synchronize()
+        got, gg = res["loglike"].cpu().numpy(), res["grad"].cpu().numpy()
+        tol = 1e-10 if prec == "fp64" else 1e-5
+        assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1)) <= tol, prec
+        sc = np.abs(wantg).max(axis=1, keepdims=True) + 1e-12
+        assert np.max(np.abs(gg - wantg) / sc) <= (1e-8 if prec == "fp64" else 1e-4), prec
+
+
+def test_status_codes_and_nan_outputs(lib):
+    P = np.array([[70, 0.3, 0.7, 1e-5], [-70, 0.3, 0.7, 1e-5], [70, np.nan, 0.7, 1e-5], [70, 0.1, 2.5, 1e-5],
+                  [70, 0.3, 0.7, -1e-5], [70, 0.0, 0.7, 0.0]])
+    z = np.tile([0.5, 1.0], P.shape[0])
+    res = lib.distances(_t(P), _t(z), None, layout="dense", outputs=("d_C", "mu"), precision="fp64")
+    torch.cuda.synchronize()
+    st = res["status"].cpu().numpy()
+    assert st.tolist() == [0, 2, 2, 1, 2, 2]
+    d = res["d_C"].cpu().numpy().reshape(-1, 2)
+    assert np.all(np.isfinite(d[0])) and np.all(np.isnan(d[1:]))
+
+
+def test_full_size_sampled_bench_configuration(lib):
+    """config2 at full size (4096 x 1024) in the benchmark's launch shape, a
+    random sample checked pair by pair against the Carlson oracle."""
+    b = workloads.config2()
+    z32 = b.z.astype(np.float32)
+    res = lib.distances(_t(b.params), _t(z32), _t(b.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp32")
+    torch.cuda.synchronize()
+    assert int(res["status"].abs().sum()) == 0
+    rng = np.random.default_rng(0)
+    idx = np.sort(rng.choice(b.nnz, 3000, replace=False))
+    rows = np.searchsorted(b.offsets, idx, side="right") - 1
+    ref = oracle.quad_distances(b.params[rows], z32[idx].astype(np.float64), np.arange(idx.size + 1))
+    sub = {n: res[n][torch.tensor(idx, device=DEV)] for n in ("d_C", "t", "X", "mu")}
+    _check(sub, ref, TOL32, "fp32", names=("d_C", "t", "X"))
+    _check({"mu": sub["mu"]}, ref, TOL32, "fp32", names=())
+
+
+def test_autotune_and_launch_count(lib):
+    b = workloads.config2(B=64, n=256, seed=3)
+    n0 = lib.launch_count()
+    t = lib.autotune(_t(b.params), _t(b.z.astype(np.float32)), _t(b.offsets), outputs=("d_C", "mu"))
+    assert t["block"] in (64, 128, 256) and t["blocks_per_sm"] >= 1 and t["ms"] > 0
+    assert lib.launch_count() > n0
