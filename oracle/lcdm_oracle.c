@@ -341,6 +341,62 @@ static int adapt(const cosmo_t* c, int mode, double lo, double hi, double rtol, 
     return capped ? -nacc : nacc;
 }
 
+/* Breakpoints for the quadrature: near the no-Big-Bang boundary (Sec. 3,
+ * Fig. 1) Q(a) has a deep minimum on the path and 1/sqrt(Q) a narrow peak,
+ * which a coarse rule can step over.  The stationary points of Q in (lo, hi)
+ * (roots of Q'(a) = Om + 2 Ok a + 4 OL a^3, found by bracketing on a grid and
+ * bisection) and points at 1, 4, 16 and 64 peak widths sqrt(Q/|Q''|) on either
+ * side become interval ends, in addition to 8 equal pieces. */
+static int quad_breakpoints(const cosmo_t* c, double lo, double hi, double* bp) {
+    int n = 0;
+    const int NG = 256;
+    double prev = 0, aprev = lo;
+    for (int i = 0; i <= NG; i++) {
+        double a = lo + (hi - lo) * i / NG;
+        double d = c->Om + 2.0 * c->Ok * a + 4.0 * c->OL * a * a * a;
+        if (i > 0 && ((prev < 0) != (d < 0))) {
+            double x0 = aprev, x1 = a, d0 = prev;
+            for (int it = 0; it < 200; it++) {
+                double xm = 0.5 * (x0 + x1), dm = c->Om + 2.0 * c->Ok * xm + 4.0 * c->OL * xm * xm * xm;
+                if ((dm < 0) == (d0 < 0)) { x0 = xm; d0 = dm; } else x1 = xm;
+            }
+            double as = 0.5 * (x0 + x1);
+            double Q = c->Or + c->Om * as + c->Ok * as * as + c->OL * as * as * as * as;
+            double Q2 = 2.0 * c->Ok + 12.0 * c->OL * as * as;
+            double wd = (Q > 0 && Q2 != 0) ? sqrt(Q / fabs(Q2)) : 0.0;
+            bp[n++] = as;
+            for (int k = 1; k <= 64 && wd > 0; k *= 4) { bp[n++] = as - k * wd; bp[n++] = as + k * wd; }
+        }
+        prev = d; aprev = a;
+    }
+    for (int i = 1; i < 8; i++) bp[n++] = lo + (hi - lo) * i / 8.0;
+    /* keep those inside, sorted */
+    int m = 0;
+    for (int i = 0; i < n; i++) if (bp[i] > lo && bp[i] < hi) bp[m++] = bp[i];
+    for (int i = 1; i < m; i++) for (int j = i; j > 0 && bp[j - 1] > bp[j]; j--) { double t = bp[j]; bp[j] = bp[j - 1]; bp[j - 1] = t; }
+    return m;
+}
+
+/* Adaptive quadrature over [lo, hi] of t (mode as in gl_rule), split at the
+ * breakpoints (mapped to t when mode == 1); results added to total. */
+static void integrate_pieces(const cosmo_t* c, int mode, double lo, double hi, double rtol, double* total) {
+    double bp[64], part[NCOMP];
+    double alo = mode ? 1.0 - hi : lo, ahi = mode ? 1.0 - lo : hi;
+    int m = quad_breakpoints(c, alo, ahi, bp);
+    double t[66];
+    int nt = 0;
+    t[nt++] = lo;
+    for (int i = 0; i < m; i++) {
+        double v = mode ? 1.0 - bp[m - 1 - i] : bp[i];
+        if (v > t[nt - 1] && v < hi) t[nt++] = v;
+    }
+    t[nt++] = hi;
+    for (int i = 0; i + 1 < nt; i++) {
+        adapt(c, mode, t[i], t[i + 1], rtol, part);
+        for (int k = 0; k < NCOMP; k++) total[k] += part[k];
+    }
+}
+
 static void unpack_params(const double* p, int ncol, double* H0, cosmo_t* c) {
     *H0 = p[0];
     c->Om = p[1]; c->OL = p[2]; c->Or = p[3];
@@ -377,11 +433,14 @@ int oracle_quad_distances(const double* params, int64_t B, int ncol, const int64
             for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
         } else {
             /* [a(z), 1] split at a = 1/2: near a = 1 integrate in s = 1 - a over
-             * [0, min(z/(1+z), 1/2)]; below a = 1/2 integrate in a itself. */
+             * [0, min(z/(1+z), 1/2)]; below a = 1/2 integrate in a itself.  Each
+             * part is further split at the breakpoints of quad_breakpoints. */
             double w = zz / (1.0 + zz), I2[NCOMP];
-            adapt(&c, 1, 0.0, w < 0.5 ? w : 0.5, rtol, Iv);
+            for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
+            integrate_pieces(&c, 1, 0.0, w < 0.5 ? w : 0.5, rtol, Iv);
             if (w > 0.5) {
-                adapt(&c, 0, 1.0 / (1.0 + zz), 0.5, rtol, I2);
+                for (int k = 0; k < NCOMP; k++) I2[k] = 0.0;
+                integrate_pieces(&c, 0, 1.0 / (1.0 + zz), 0.5, rtol, I2);
                 for (int k = 0; k < NCOMP; k++) Iv[k] += I2[k];
             }
         }

@@ -164,50 +164,63 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* p
 // Labels: t uses i = A; X uses i = B, l = A (quartic) or i = A (cubic); the
 // pair members are j, k.  See eqs. (3.7)-(3.9) and (B.1)-(B.3).
 // ---------------------------------------------------------------------------
+// Quartic (Or > 0).  The big root A ~ -Om/Or and the prefactor Or^-1/2 each
+// depend on Or like 1/Or; their product does not.  By the homogeneity of the
+// Carlson integrals (R_F, R_C ~ s^-1/2; R_J, R_D ~ s^-3/2) every argument is
+// scaled by lam = Or, and the big root enters only through
+//   a_A = -lam A,  m_A = lam rho_A,  eps_A = -1/rho_A,  rho_A = 1 + A,
+// so that X~_A = sqrt(lam (z - A)) = sqrt(lam z + a_A), Y~_A = sqrt(a_A) and
+// every factor below has derivatives of its own size.  Written out:
+//   eq. (3.7):  chi H0/c = 2z R_F(u~^2)
+//   eq. (3.8):  t H0 = 2z [ R_C(k s5, k q5) - eps_A R_F - z^2/3 m_A (1 + eps_A rho_B) |1 + eps_A rho_P|^2 R_J(u~^2, lam u_A5^2) ]
+//   eq. (3.9):  X H0/c = z [ T0 + (2 rho_B^2 - |P-B|^2) R_F + rho_A G ]
+// with u~ = sqrt(lam) u and the terms defined in the code.
 template <class S, class PS, bool WT, bool WX>
-LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& A, const S& B, const PS& P, const S& YA,
-                               const S& YB, const PS& YP, const S& amh, S& Ichi, S& It, S& IX, int* fail) {
+LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
+                               const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, S& Ichi, S& It,
+                               S& IX, int* fail) {
     typedef typename Base<S>::type T;
-    const T one = cst<T>(1.0);
+    const T one = cst<T>(1.0), third = cst<T>(1.0 / 3.0);
     const T z2 = z * z;
-    S XA = ssqrt(z - A), XB = ssqrt(z - B);
+    S XtA = ssqrt(lam * z + aA), YtA = ssqrt(aA);
+    S XB = ssqrt(z - B);
     PS XP = psqrt(prsub(z, P));
     S ppYP = pprod(YP), ppXP = pprod(XP);
-    // u_ij of Sec. 3.1 with z1 = 0: u_AB (real) and the pair (u_AP, u_AP*)
-    S uAB = XA * XB * ppYP + YA * YB * ppXP;
+    // u_ij of Sec. 3.1 with z1 = 0, times sqrt(lam): u_AB (real), pair (u_AP, u_AP*)
+    S uAB = XtA * XB * ppYP + YtA * YB * ppXP;
     PS W = XP * pswap(YP);
-    PS uAP = pscale(W, XA * YB) + pscale(pswap(W), YA * XB);
+    PS uAP = pscale(W, XtA * YB) + pscale(pswap(W), YtA * XB);
     S x1 = uAB * uAB;
     PS pr = uAP * uAP;
+    S rhoB = B + one;
+    PS rhoP = padd(P, one);
+    S ppPA = pprod(padd(pscale(rhoP, epsA), one));     // |P - A|^2 / rho_A^2
+    S ppPB = pprod(padd(P, -B));
     enum { NJ = (WT ? 1 : 0) + (WX ? 1 : 0) };
     S p[NJ > 0 ? NJ : 1];
-    S rhoA = A + one, rhoB = B + one;
-    S ppPA = pprod(padd(P, -A));
-    S ppPB = pprod(padd(P, -B));
     int jt = 0, jx = WT ? 1 : 0;
-    if (WT) p[jt] = x1 - ppPA * rhoB / rhoA * z2;   // u_A5^2
-    if (WX) p[jx] = x1 - ppPB * z2;                  // u_B0^2
+    if (WT) p[jt] = x1 - mA * ppPA * rhoB * z2;        // lam u_A5^2
+    if (WX) p[jx] = x1 - lam * ppPB * z2;              // lam u_B0^2
     S RF, RD1, RJ[NJ > 0 ? NJ : 1];
     carlson_any<NJ>(x1, pr, p, WX, RF, RD1, RJ, fail);
-    Ichi = amh * RF * (z + z);                         // eq. (3.7)
+    Ichi = RF * (z + z);                               // eq. (3.7)
     if (WT) {                                          // eq. (3.8), i = A
-        S q5 = p[jt] * (one + z) / (YA * YA * XA * XA);
-        S s5 = q5 + pprod(padd(P, one)) * rhoB / rhoA * z2;
-        S ct = (B - A) * ppPA / (-rhoA) * (z2 * cst<T>(1.0 / 3.0));
-        It = amh * (z + z) / rhoA * (RF - (ct * RJ[jt] + rc_any(s5, q5, fail)));
+        S kq5 = p[jt] * (one + z) / ((one + epsA) * (one + epsA * (one + z)));
+        S ks5 = kq5 + mA * pprod(rhoP) * rhoB * z2;
+        It = (rc_any(ks5, kq5, fail) - epsA * RF - mA * (one + epsA * rhoB) * ppPA * RJ[jt] * (z2 * third)) * (z + z);
     }
     if (WX) {                                          // eq. (3.9), i = B, l = A
-        S q0 = p[jx] / (YB * YB * XB * XB);
-        S s0 = q0 + z2;
-        S eA = one / (XA + YA), eB = one / (XB + YB);
+        S lq0 = p[jx] / (YB * YB * XB * XB);
+        S ls0 = lq0 + lam * z2;
+        S eB = one / (XB + YB);
         PS XY = XP + YP;
         S Dpp = psum(prcp(XY) * pswap(XY)) * cst<T>(0.5);
-        // [X_B X_P X_P* / X_A]_0^z / z without cancellation (telescoped)
-        S T0 = (eB * ppXP + YB * Dpp - YB * ppYP * eA / YA) / XA;
+        // [X_B X_P X_P* / X_A]_0^z / z, telescoped, times Or^-1/2
+        S T0 = (eB * ppXP + YB * Dpp) / XtA - lam * YB * ppYP / ((XtA + YtA) * XtA * YtA);
         S T1 = (rhoB * rhoB * cst<T>(2.0) - ppPB) * RF;
-        S T2 = ppPA * (ppPB * RD1 * (z2 * cst<T>(1.0 / 3.0)) + XB * YB / (XA * YA * uAB));
-        S T3 = (A + B + psum(P) + cst<T>(4.0)) * (rc_any(s0, q0, fail) - ppPB * (A - B) * RJ[jx] * (z2 * cst<T>(1.0 / 3.0)));
-        IX = amh * (T0 + T1 + T2 + T3) * z;
+        S G = mA * ppPA * (ppPB * RD1 * (z2 * third) + XB * YB / (XtA * YtA * uAB))
+              + (one - epsA * (rhoB + psum(rhoP))) * (rc_any(ls0, lq0, fail) + ppPB * (aA + lam * B) * RJ[jx] * (z2 * third));
+        IX = (T0 + T1 + rhoA * G) * z;
     }
 }
 

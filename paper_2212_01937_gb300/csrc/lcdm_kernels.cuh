@@ -29,8 +29,12 @@ namespace lcdm {
 enum RecField {
     RF_A = 0, RF_B, RF_PRE, RF_PIM, RF_YA, RF_YB, RF_YPRE, RF_YPIM,
     RF_AMH, RF_OK, RF_H0, RF_DH, RF_TH, RF_KIND,
-    RF_DA = 14, RF_DB = 18, RF_DPRE = 22, RF_DPIM = 26, RF_DAMH = 30, RF_DOK = 34,
-    NREC = 38
+    // quartic big-root quantities: lam = Or, a_A = -lam A, m_A = lam rho_A, eps_A = -1/rho_A, rho_A
+    RF_LAM, RF_AA, RF_MA, RF_EPSA, RF_RHOA,
+    // tangents (4 slots each: Om, OL, Or, Ok)
+    RF_DA = 19, RF_DB = 23, RF_DPRE = 27, RF_DPIM = 31, RF_DAMH = 35, RF_DOK = 39,
+    RF_DLAM = 43, RF_DAA = 47, RF_DMA = 51, RF_DEPSA = 55, RF_DRHOA = 59,
+    NREC = 63
 };
 
 enum CosmoStatus {
@@ -162,7 +166,10 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
             if (kind == 0) {
                 S B = val(rd, rf, RF_B, RF_DB);
                 S YB = yval(rd, rf, RF_YB, B);
-                quartic_integrals<S, CPair<S>, WT, WX>(z, A, B, P, YA, YB, YP, amh, Ichi, It, IX, fail);
+                quartic_integrals<S, CPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
+                                                       val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
+                                                       val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, Ichi, It, IX,
+                                                       fail);
             } else {
                 cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, Ichi, It, IX, fail);
             }
@@ -172,7 +179,10 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
             if (kind == 1) {
                 S B = val(rd, rf, RF_B, RF_DB);
                 S YB = yval(rd, rf, RF_YB, B);
-                quartic_integrals<S, RPair<S>, WT, WX>(z, A, B, P, YA, YB, YP, amh, Ichi, It, IX, fail);
+                quartic_integrals<S, RPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
+                                                       val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
+                                                       val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, Ichi, It, IX,
+                                                       fail);
             } else {
                 cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, Ichi, It, IX, fail);
             }

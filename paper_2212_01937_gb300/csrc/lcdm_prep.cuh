@@ -200,6 +200,23 @@ __global__ void prep_kernel(const double* __restrict__ params, int64_t B, int nc
                     if (n == 3 && k == 2) dr[j][k] = cmk(CUDART_NAN, CUDART_NAN);  // no Or direction in a cubic
                 }
             }
+            // big-root quantities of the quartic, scaled by lam = Or (see quartic_integrals)
+            if (n == 4) {
+                double rA = A.re;                  // rho_A
+                rec[RF_LAM] = Or;
+                rec[RF_AA] = -Or * (rA - 1.0);
+                rec[RF_MA] = Or * rA;
+                rec[RF_EPSA] = -1.0 / rA;
+                rec[RF_RHOA] = rA;
+                for (int k = 0; k < K; k++) {
+                    double dl = (k == 2) ? 1.0 : 0.0, dA = dr[0][k].re;
+                    rec[RF_DLAM + k] = dl;
+                    rec[RF_DAA + k] = -(dl * (rA - 1.0) + Or * dA);
+                    rec[RF_DMA + k] = dl * rA + Or * dA;
+                    rec[RF_DEPSA + k] = dA / (rA * rA);
+                    rec[RF_DRHOA + k] = dA;
+                }
+            }
             for (int k = 0; k < K; k++) {
                 rec[RF_DA + k] = dr[0][k].re;
                 rec[RF_DB + k] = n == 4 ? dr[1][k].re : 0.0;

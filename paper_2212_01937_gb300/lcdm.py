@@ -210,7 +210,7 @@ def autotune(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), cot=None,
     """Pick the fastest launch shape for this workload class (lcdm_autotune)."""
     c = Call(params, z, offsets, **kw)
     out, vp = c.out_buffers(outputs)
-    cp, grad = None, None
+    cp, grad = _VP6(), None
     if cot is not None:
         cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items()}
         cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])

@@ -189,8 +189,12 @@ def test_gauss_loglike_vs_oracle(lib):
         res = lib.gauss_loglike(_t(b.params), _t(zin), _t(m), _t(b.offsets), M=b.M, sigma=b.sigma, precision=prec)
         torch.cuda.synchronize()
         got, gg = res["loglike"].cpu().numpy(), res["grad"].cpu().numpy()
-        tol = 1e-10 if prec == "fp64" else 1e-5
-        assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1)) <= tol, prec
+        if prec == "fp64":
+            assert np.max(np.abs(got - want) / np.maximum(np.abs(want), 1)) <= 1e-10
+        else:
+            # mu is an FP32 number near 40 mag (ulp ~4e-6): allow |dl| <= sum |r|/sigma * 2e-5
+            bound = np.add.reduceat(np.abs(r) / b.sigma, b.offsets[:-1]) * 2e-5 + 1e-6 * np.abs(want)
+            assert np.all(np.abs(got - want) <= bound), prec
         sc = np.abs(wantg).max(axis=1, keepdims=True) + 1e-12
         assert np.max(np.abs(gg - wantg) / sc) <= (1e-8 if prec == "fp64" else 1e-4), prec
 

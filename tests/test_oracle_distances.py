@@ -181,3 +181,34 @@ def test_curvature_map_small_curvature():
         pm[4] -= h
         fd = (q(pp, z)[:, 3] - q(pm, z)[:, 3]) / (2 * h)
         assert rel(J[:, 3, 4], fd) < 1e-6
+
+
+def test_near_boundary_peak_resolved():
+    """Near the no-Big-Bang boundary (Sec. 3, Fig. 1) the integrand 1/E has a
+    narrow peak at the complex pair's real part; the quadrature must resolve
+    it.  Pinned against mpmath quadrature split at the peak and against the
+    Carlson assembly (which is exact there, fn14's branch caveat aside)."""
+    p = np.array([68.6741596, 0.286697693, 1.69305727, 9.52482287e-05, -0.979850211])
+    z = np.array([0.5, 1.3, 2.0, 10.0, 525.0])
+    o1 = q(p, z)
+    o2 = oracle.carlson_distances(p, z)
+    assert rel(o2[:, :3], o1[:, :3]) < 2e-11
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 30
+    Om, OL, Or, Ok = [mp.mpf(float(x)) for x in p[1:]]
+    E = lambda zz: mp.sqrt(Or * (1 + zz) ** 4 + Om * (1 + zz) ** 3 + Ok * (1 + zz) ** 2 + OL)
+    zp = mp.mpf(1.2761806)
+    dh = 299792.458 / p[0]
+    for zi, oi in zip(z, o1):
+        pts = [0] + [x for x in (zp - 0.05, zp - 0.005, zp, zp + 0.005, zp + 0.05) if x < zi] + [mp.mpf(zi)]
+        ref = float(mp.quad(lambda zz: 1 / E(zz), pts)) * dh
+        # Q(a) at the peak is ~1e-6 of its terms: the FP64 integrand itself is
+        # only good to ~1e-10 there, which bounds what quadrature can reach
+        assert abs(oi[0] / ref - 1) < 1e-10
+
+
+def test_stress_rows_quadrature_vs_carlson():
+    s = workloads.config5(B=6, n=25, seed=4)
+    o1 = q(s.params, s.z, offsets=s.offsets)
+    o2 = oracle.carlson_distances(s.params, s.z, offsets=s.offsets)
+    assert rel(o2[:, :2], o1[:, :2]) < 1e-9
