@@ -28,9 +28,9 @@
  *            n redshifts z[n]; pair (b, i) has index b*n + i.
  *            npairs = n (CSR) or B*n (DENSE, SHARED).
  *   dtype    precision LCDM_FP64: z, outputs, cotangents, Jacobians and
- *            m_obs are float64.  LCDM_FP32_MIXED: they are float32; the root
- *            solve and all per-cosmology reductions are FP64 and X (and the
- *            tangent of t) is evaluated in double-float arithmetic.
+ *            m_obs are float64 and every step is FP64.  LCDM_FP32_MIXED: they
+ *            are float32 and the per-pair arithmetic is FP32; the root solve
+ *            and all per-cosmology reductions stay FP64.
  *   units    d_C, d_M, d_L, X in Mpc; t in Gyr; mu in magnitudes.
  *   memory   every pointer argument except opts is a DEVICE pointer owned by
  *            the caller; the library allocates nothing.  Scratch comes from

@@ -35,27 +35,37 @@ template <class T> LCDM_HD T rc_any(T x, T y, int* fail) {
     return rc_value(x, y, fail);
 }
 
+// The R_J tracks are given by h_j = p_j - x1 (their distance from the single
+// argument): the callers form h_j directly, without cancellation.
 template <int NJ, class T, class PT>
-LCDM_HD void carlson_any(T x1, PT pr, const T* p, bool needRD1, T& RF, T& RD1, T* RJ, int* fail) {
+LCDM_HD void carlson_any(T x1, PT pr, const T* h, bool needRD1, T& RF, T& RD1, T* RJ, int* fail, T* DJ = 0) {
     T tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1];
     bool pv[NJ > 0 ? NJ : 1];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        pv[j] = sval(p[j]) < 0;
+        T p = x1 + h[j];
+        pv[j] = sval(p) < 0;
         if (pv[j]) {
-            q[j] = -p[j];
+            q[j] = -p;
             s[j] = (x1 * (psum(pr) + q[j]) - pprod(pr)) / (x1 + q[j]);
             if (!(sval(s[j]) > 0)) *fail = 2;
             tr[j] = s[j];
         } else {
-            tr[j] = p[j];
+            tr[j] = p;
         }
     }
-    if (needRD1) {
+    if (DJ && NJ > 0 && !pv[NJ - 1]) {
+        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, true>(x1, pr, tr, fail, h[NJ > 0 ? NJ - 1 : 0]);
+        RF = R.RF; RD1 = R.RD1;
+#pragma unroll
+        for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
+        *DJ = R.DJ;
+    } else if (needRD1) {
         DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true>(x1, pr, tr, fail);
         RF = R.RF; RD1 = R.RD1;
 #pragma unroll
         for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
+        if (DJ && NJ > 0) *DJ = (R.RJ[NJ - 1] - RD1) / h[NJ - 1];
     } else {
         DupResult<T, NJ, PT> R = carlson_dup<T, NJ, false>(x1, pr, tr, fail);
         RF = R.RF; RD1 = RF;
@@ -69,6 +79,7 @@ LCDM_HD void carlson_any(T x1, PT pr, const T* p, bool needRD1, T& RF, T& RD1, T
             T rc = rc_value(xy + sq, sq, fail);
             RJ[j] = ((s[j] - x1) * RJ[j] - cst<T>(3.0) * RF + cst<T>(3.0) * ssqrt(x1 * xy / (xy + sq)) * rc)
                     / (q[j] + x1);
+            if (DJ && j == NJ - 1) *DJ = (RJ[j] - RD1) / h[j];
         }
     }
 }
@@ -92,78 +103,164 @@ template <class T, int K> LCDM_HD Dual<T, K> rc_any(const Dual<T, K>& x, const D
     return rc_dual_pos(x, y, fail);
 }
 
+// Relative spread of the arguments below which the derivative formulas lose
+// too many digits (they divide by differences of the arguments): there the
+// tangents are carried through the duplication sequence itself.
+template <class T> struct Spread;
+template <> struct Spread<float> { static LCDM_HD float s0() { return 0.5f; } };
+template <> struct Spread<double> { static LCDM_HD double s0() { return 0.05; } };
+template <> struct Spread<df64> { static LCDM_HD df64 s0() { return mkdf(0.1f); } };
+
 template <int NJ, class T, int K, class PD>
-LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* p, bool needRD1, Dual<T, K>& RF,
-                         Dual<T, K>& RD1, Dual<T, K>* RJ, int* fail) {
+LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h, bool needRD1, Dual<T, K>& RF,
+                         Dual<T, K>& RD1, Dual<T, K>* RJ, int* fail, Dual<T, K>* DJ = 0) {
     typedef Dual<T, K> D;
     typedef typename PairVal<PD>::type PT;
     const T xv = x1.v;
     const PT prv = pval(pr);
-    D tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1];
+    D tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1], hh[NJ > 0 ? NJ : 1];
     T trv[NJ > 0 ? NJ : 1];
     bool pv[NJ > 0 ? NJ : 1];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        pv[j] = sval(p[j].v) < 0;
+        D p = x1 + h[j];
+        pv[j] = sval(p.v) < 0;
         if (pv[j]) {
-            q[j] = -p[j];
+            q[j] = -p;
             s[j] = (x1 * (psum(pr) + q[j]) - pprod(pr)) / (x1 + q[j]);
             if (!(sval(s[j].v) > 0)) *fail = 2;
             tr[j] = s[j];
+            hh[j] = s[j] - x1;
         } else {
-            tr[j] = p[j];
+            tr[j] = p;
+            hh[j] = h[j];
         }
         trv[j] = tr[j].v;
     }
-    DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true>(xv, prv, trv, fail);
-    // R_F, eq. (2.10)
-    RF.v = R.RF;
+    const bool ddl = DJ && NJ > 0 && !pv[NJ > 0 ? NJ - 1 : 0];
+    // spread of the arguments around their mean
+    T mu = xv + psum(prv);
 #pragma unroll
-    for (int k = 0; k < K; k++) RF.d[k] = (R.RD1 * x1.d[k] + pdot_k(R.RDp, pr, k)) * cst<T>(-1.0 / 6.0);
-    // R_D(x2, x3, x1)
-    if (needRD1) {
-        PT dpair = pscale(prsub(R.RD1, R.RDp) / prsub(xv, prv), cst<T>(0.5));
-        T d1 = (cst<T>(-1.5) * R.RD1 - pdot(prv, dpair)) / xv;
-        RD1.v = R.RD1;
+    for (int j = 0; j < NJ; j++) mu = mu + trv[j];
+    mu = mu * cst<T>(1.0 / (3 + NJ));
+    T dev2 = (xv - mu) * (xv - mu), pd2 = pdev2(prv, mu);
+    if (sval(pd2) > sval(dev2)) dev2 = pd2;
 #pragma unroll
-        for (int k = 0; k < K; k++) RD1.d[k] = d1 * x1.d[k] + pdot_k(dpair, pr, k);
+    for (int j = 0; j < NJ; j++) {
+        T dj = (trv[j] - mu) * (trv[j] - mu);
+        if (sval(dj) > sval(dev2)) dev2 = dj;
     }
-    if (NJ > 0) {
-        // 6 R_G = sum_m x_m (e1 - x_m) R_D_m
-        T RG = (xv * psum(prv) * R.RD1 + pdot(R.RDp, prv * padd(pswap(prv), xv))) * cst<T>(1.0 / 6.0);
-        T sq3 = ssqrt(xv) * pprod(psqrt(prv));
+    T lim = Spread<T>::s0() * mu;
+    const bool close = sval(dev2) < sval(lim * lim);
+    D Jd[NJ > 0 ? NJ : 1];
+    if (close) {
+        // tangents through the duplication sequence (arguments nearly equal)
+        DupResult<D, NJ, PD> R = ddl ? carlson_dup<D, NJ, true, PD, true>(x1, pr, tr, fail, hh[NJ > 0 ? NJ - 1 : 0])
+                                     : carlson_dup<D, NJ, true, PD>(x1, pr, tr, fail);
+        RF = R.RF;
+        RD1 = R.RD1;
 #pragma unroll
-        for (int j = 0; j < NJ; j++) {
-            const T pt = trv[j], J = R.RJ[j];
-            const T ipx = cst<T>(1.0) / (pt - xv);
-            const PT ipp = prcp(prsub(pt, prv));
-            T d1 = (J - R.RD1) * ipx * cst<T>(0.5);
-            PT dpair = pscale(prsub(J, R.RDp) * ipp, cst<T>(0.5));
-            T dp = cst<T>(1.5) * ((pt * pt * R.RF - cst<T>(2.0) * pt * RG + sq3) * ipx * pprod(ipp) / pt
-                                  - (ipx + psum(ipp)) * J * cst<T>(1.0 / 3.0));
-            D Jd;
-            Jd.v = J;
+        for (int j = 0; j < NJ; j++) Jd[j] = R.RJ[j];
+        if (ddl) *DJ = R.DJ;
+    } else {
+        DupResult<T, NJ, PT> R = ddl ? carlson_dup<T, NJ, true, PT, true>(xv, prv, trv, fail, hh[NJ > 0 ? NJ - 1 : 0].v)
+                                     : carlson_dup<T, NJ, true, PT>(xv, prv, trv, fail);
+        // R_F, eq. (2.10)
+        RF.v = R.RF;
 #pragma unroll
-            for (int k = 0; k < K; k++) Jd.d[k] = d1 * x1.d[k] + pdot_k(dpair, pr, k) + dp * tr[j].d[k];
-            if (!pv[j]) {
-                RJ[j] = Jd;
-            } else {
-                D xy = pprod(pr), sq = s[j] * q[j];
-                D rc = rc_dual_pos(xy + sq, sq, fail);
-                RJ[j] = ((s[j] - x1) * Jd - RF * cst<T>(3.0) + ssqrt(x1 * xy / (xy + sq)) * rc * cst<T>(3.0))
-                        / (q[j] + x1);
+        for (int k = 0; k < K; k++) RF.d[k] = (R.RD1 * x1.d[k] + pdot_k(R.RDp, pr, k)) * cst<T>(-1.0 / 6.0);
+        // R_D(x2, x3, x1): dR_D(x,y,z)/dx = (R_D(x,y,z) - R_D(y,z,x)) / (2 (z - x)); x1 by homogeneity
+        if (needRD1) {
+            PT dpair = pscale(prsub(R.RD1, R.RDp) / prsub(xv, prv), cst<T>(0.5));
+            T d1 = (cst<T>(-1.5) * R.RD1 - pdot(prv, dpair)) / xv;
+            RD1.v = R.RD1;
+#pragma unroll
+            for (int k = 0; k < K; k++) RD1.d[k] = d1 * x1.d[k] + pdot_k(dpair, pr, k);
+        }
+        if (NJ > 0) {
+            // 6 R_G = sum_m x_m (e1 - x_m) R_D_m
+            T RG = (xv * psum(prv) * R.RD1 + pdot(R.RDp, prv * padd(pswap(prv), xv))) * cst<T>(1.0 / 6.0);
+            T sq3 = ssqrt(xv) * pprod(psqrt(prv));
+#pragma unroll
+            for (int j = 0; j < NJ; j++) {
+                const T pt = trv[j], J = R.RJ[j], hv = hh[j].v;
+                const PT ipp = prcp(prsub(pt, prv));
+                // dR_J/dx_m for the pair members, eq. (2.11)
+                PT dpair = pscale(prsub(J, R.RDp) * ipp, cst<T>(0.5));
+                // (p - x1) dR_J/dp from eq. (2.12), multiplied through by (p - x1)
+                T hdp = cst<T>(1.5) * ((pt * pt * R.RF - cst<T>(2.0) * pt * RG + sq3) * pprod(ipp) / pt
+                                       - (cst<T>(1.0) + hv * psum(ipp)) * J * cst<T>(1.0 / 3.0));
+                // (d/dx1 + d/dp) R_J from homogeneity (degree -3/2); then
+                // dR_J = (d1 + dp) R_J dx1 + sum dR_J/dx_m dx_m + dR_J/dp d(p - x1)
+                T diag = (cst<T>(-1.5) * J - pdot(prv, dpair) - hdp) / xv;
+                T dph = hdp / hv;
+                Jd[j].v = J;
+#pragma unroll
+                for (int k = 0; k < K; k++) Jd[j].d[k] = diag * x1.d[k] + pdot_k(dpair, pr, k) + dph * hh[j].d[k];
+                if (ddl && j == NJ - 1) {
+                    // Delta = (R_J(x1 + h) - R_D(x2,x3,x1)) / h and its tangent from the
+                    // divided differences of eqs. (2.11)-(2.12):
+                    //  dDelta/dx_m = [Delta (x1 - x_m) - (R_D1 - R_Dm)] / (2 (p - x_m)(x1 - x_m))
+                    //  dDelta/dx1  = [-3/2 Delta - sum x_m dDelta/dx_m - dR_J/dp] / x1
+                    //  h dDelta/dh = dR_J/dp - Delta,  dR_J/dp = -Delta/2 + 3/2 Br
+                    const T Dl = R.DJ;
+                    PT xm = prsub(xv, prv);
+                    PT dxm = pscale((pscale(xm, Dl) - prsub(R.RD1, R.RDp)) / (prsub(pt, prv) * xm), cst<T>(0.5));
+                    const T S0 = psum(xm), P0 = pprod(xm);
+                    const T beta = cst<T>(1.0) / xv + (S0 + hv) / P0 + hv * (S0 + hv) / (xv * P0);
+                    const T Br = -(R.RD1 * cst<T>(1.0 / 3.0)) * beta / (cst<T>(1.0) + hv * beta)
+                                 + ((cst<T>(2.0) * xv + hv) * R.RF - cst<T>(2.0) * RG) * pprod(ipp) / pt
+                                 - psum(ipp) * J * cst<T>(1.0 / 3.0);
+                    const T dpR = cst<T>(-0.5) * Dl + cst<T>(1.5) * Br;
+                    const T d1 = (cst<T>(-1.5) * Dl - pdot(prv, dxm) - dpR) / xv;
+                    const T dhh = cst<T>(1.5) * (Br - Dl);
+                    D dd;
+                    dd.v = Dl;
+#pragma unroll
+                    for (int k = 0; k < K; k++)
+                        dd.d[k] = d1 * x1.d[k] + pdot_k(dxm, pr, k) + dhh * (hh[j].d[k] / hv);
+                    *DJ = dd;
+                }
             }
         }
     }
+    // principal values (the tracks ran at s_j) and the divided difference fallback
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        if (!pv[j]) {
+            RJ[j] = Jd[j];
+        } else {
+            D xy = pprod(pr), sq = s[j] * q[j];
+            D rc = rc_dual_pos(xy + sq, sq, fail);
+            RJ[j] = ((s[j] - x1) * Jd[j] - RF * cst<T>(3.0) + ssqrt(x1 * xy / (xy + sq)) * rc * cst<T>(3.0))
+                    / (q[j] + x1);
+        }
+    }
+    if (DJ && NJ > 0 && !ddl) *DJ = (RJ[NJ - 1] - RD1) / h[NJ - 1];
 }
 
-// ---------------------------------------------------------------------------
-// Distance integrals, dimensionless: I_chi = chi H0/c, I_t = t H0, I_X = X H0/c,
-// each including the alpha_m^-1/2 prefactor.  z1 = 0, z2 = z.
-// Roots in z: A (real), B (real, quartic only), the pair P; Y = sqrt(-root).
-// Labels: t uses i = A; X uses i = B, l = A (quartic) or i = A (cubic); the
-// pair members are j, k.  See eqs. (3.7)-(3.9) and (B.1)-(B.3).
-// ---------------------------------------------------------------------------
+// Phi(w) = [R_C(1, 1-w) - (1-w)^-1/2] / w: the part of R_C(y + d, y) - y^-1/2
+// that is linear in w = d / (y + d), as a series for small w (coefficients
+// 1/(2n+1) - C(2n,n)/4^n, n >= 1) and directly otherwise.
+template <class S> LCDM_HD S phi_rc(const S& w, int* fail) {
+    typedef typename Base<S>::type T;
+    const int NT = sizeof(T) == 4 ? 9 : 17;
+    if (sval(vof(w)) <= 0.1) {
+        double cs[17];
+        double bn = 1.0;
+        for (int n = 1; n <= NT; n++) {
+            bn *= (2.0 * n - 1.0) / (2.0 * n);
+            cs[n - 1] = 1.0 / (2.0 * n + 1.0) - bn;
+        }
+        S acc = w * cst<T>(0.0) + cst<T>(cs[NT - 1]);
+        for (int n = NT - 1; n >= 1; n--) acc = acc * w + cst<T>(cs[n - 1]);
+        return acc;
+    }
+    S one_w = cst<T>(1.0) - w;
+    S one = one_w + w;   // 1 with the type of w
+    return (rc_any(one, one_w, fail) - one / ssqrt(one_w)) / w;
+}
+
 // Quartic (Or > 0).  The big root A ~ -Om/Or and the prefactor Or^-1/2 each
 // depend on Or like 1/Or; their product does not.  By the homogeneity of the
 // Carlson integrals (R_F, R_C ~ s^-1/2; R_J, R_D ~ s^-3/2) every argument is
@@ -199,28 +296,46 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     enum { NJ = (WT ? 1 : 0) + (WX ? 1 : 0) };
     S p[NJ > 0 ? NJ : 1];
     int jt = 0, jx = WT ? 1 : 0;
-    if (WT) p[jt] = x1 - mA * ppPA * rhoB * z2;        // lam u_A5^2
-    if (WX) p[jx] = x1 - lam * ppPB * z2;              // lam u_B0^2
-    S RF, RD1, RJ[NJ > 0 ? NJ : 1];
-    carlson_any<NJ>(x1, pr, p, WX, RF, RD1, RJ, fail);
+    if (WT) p[jt] = -(mA * ppPA * rhoB * z2);          // lam u_A5^2 - x1
+    if (WX) p[jx] = -(lam * ppPB * z2);                // lam u_B0^2 - x1
+    S RF, RD1, RJ[NJ > 0 ? NJ : 1], DJ;
+    carlson_any<NJ>(x1, pr, p, WX, RF, RD1, RJ, fail, WX ? &DJ : (S*)0);
     Ichi = RF * (z + z);                               // eq. (3.7)
     if (WT) {                                          // eq. (3.8), i = A
-        S kq5 = p[jt] * (one + z) / ((one + epsA) * (one + epsA * (one + z)));
+        S kq5 = (x1 + p[jt]) * (one + z) / ((one + epsA) * (one + epsA * (one + z)));
         S ks5 = kq5 + mA * pprod(rhoP) * rhoB * z2;
         It = (rc_any(ks5, kq5, fail) - epsA * RF - mA * (one + epsA * rhoB) * ppPA * RJ[jt] * (z2 * third)) * (z + z);
     }
     if (WX) {                                          // eq. (3.9), i = B, l = A
-        S lq0 = p[jx] / (YB * YB * XB * XB);
-        S ls0 = lq0 + lam * z2;
+        // The l = A part of (3.9), rho_A G, is a sum of O(1) terms that cancel to
+        // O(lam): written out so that every term is O(1) by itself:
+        //   G1 + G4 = z^2/3 |P-B|^2 [c (a_A + lam B) h0 Delta_J + E1 R_D1],
+        //   G2 + G3 = c [R_C(y + d, y) - y^-1/2] + c Y_B X_B Num / (...) + E1 Y_B X_B / (X~_A Y~_A u~),
+        // with h0 = -lam z^2 |P-B|^2, Delta_J = (R_J(x1 + h0) - R_D) / h0, y = lam q_B0^2,
+        // d = lam z^2, E1 and Num exact polynomials carrying a factor lam, and
+        // c = 1 - eps_A (rho_B + rho_P + rho_P*).
+        S p0 = x1 + p[jx];                                    // lam u_B0^2
+        S y = p0 / (YB * YB * XB * XB);                       // lam q_B0^2
+        S dl = lam * z2;                                      // lam (s_B0^2 - q_B0^2)
+        S yd = y + dl;
+        S Phi = phi_rc(dl / yd, fail);
         S eB = one / (XB + YB);
         PS XY = XP + YP;
         S Dpp = psum(prcp(XY) * pswap(XY)) * cst<T>(0.5);
         // [X_B X_P X_P* / X_A]_0^z / z, telescoped, times Or^-1/2
         S T0 = (eB * ppXP + YB * Dpp) / XtA - lam * YB * ppYP / ((XtA + YtA) * XtA * YtA);
         S T1 = (rhoB * rhoB * cst<T>(2.0) - ppPB) * RF;
-        S G = mA * ppPA * (ppPB * RD1 * (z2 * third) + XB * YB / (XtA * YtA * uAB))
-              + (one - epsA * (rhoB + psum(rhoP))) * (rc_any(ls0, lq0, fail) + ppPB * (aA + lam * B) * RJ[jx] * (z2 * third));
-        IX = (T0 + T1 + rhoA * G) * z;
+        S Srho = psum(rhoP), Qrho = pprod(rhoP);
+        S c = one - epsA * (rhoB + Srho);
+        S aB = aA + lam * B;
+        S rE1 = -(mA * (Srho * cst<T>(2.0) + epsA * (Qrho + rhoB * rhoB + rhoB * Srho)));   // rho_A E1
+        S XYu = XtA * YtA * uAB;
+        S sp0 = ssqrt(p0);
+        S rNum = mA * (x1 * (aA * (z - B * cst<T>(2.0)) - lam * B * B) + aB * aB * ppPB * z2);   // rho_A Num
+        S rPart1 = mA * z2 / yd * Phi / ssqrt(yd);            // rho_A [R_C(y+d, y) - y^-1/2]
+        S rG = ppPB * (z2 * third) * (rE1 * RD1 - c * aB * mA * ppPB * DJ * z2)
+               + c * rPart1 + c * YB * XB * rNum / (sp0 * XYu * (XYu + aB * sp0)) + rE1 * XB * YB / XYu;
+        IX = (T0 + T1 + rG) * z;
     }
 }
 
@@ -242,13 +357,13 @@ LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, 
     enum { NJ = WT ? 1 : 0 };
     S p[1];
     S rhoA = A + one;
-    if (WT) p[0] = x1 + rhoA * z2;                     // u_A5^2
+    if (WT) p[0] = rhoA * z2;                          // u_A5^2 - x1
     S RF, RD1, RJ[1];
     carlson_any<NJ>(x1, pr, p, WX, RF, RD1, RJ, fail);
     Ichi = amh * RF * (z + z);                         // eq. (B.1)
     if (WT) {                                          // eq. (B.2)
         S s5 = YA * ppYP * (one + z) + XA * ppXP;
-        S q5 = p[0] * (one + z);
+        S q5 = (x1 + p[0]) * (one + z);
         It = amh * (z + z) * (RJ[0] * (z2 * cst<T>(1.0 / 3.0)) + rc_any(s5 * s5, q5, fail));
     }
     if (WX) {                                          // eq. (B.3), i = A

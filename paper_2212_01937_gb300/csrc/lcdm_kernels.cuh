@@ -44,7 +44,7 @@ enum CosmoStatus {
 // ------------------------------------------------------------ observables ---
 // S_k(D): sinh / sin form, or its Taylor series in u = Ok D^2 near flatness,
 // with dS/dD and dS/dOk ([59] eqs. 13.47, 13.57 as cited in Sec. 2.1.1).
-template <class T> __device__ __forceinline__ void curv_map(T D, T Ok, T& S, T& SD, T& Sk) {
+template <class T> LCDM_HD void curv_map(T D, T Ok, T& S, T& SD, T& Sk) {
     T u = Ok * D * D;
     if (fabs(u) < (T)0.05) {
         // coefficients 1/(2n+1)!, 1/(2n)!
@@ -102,10 +102,10 @@ template <> struct IO<float> { typedef float type; };
 template <> struct IO<double> { typedef double type; };
 
 // value of a record field in the pass type
-template <class T> __device__ __forceinline__ T recv(const double* rd, const float2* rf, int i);
-template <> __device__ __forceinline__ double recv<double>(const double* rd, const float2*, int i) { return rd[i]; }
-template <> __device__ __forceinline__ float recv<float>(const double*, const float2* rf, int i) { return rf[i].x; }
-template <> __device__ __forceinline__ df64 recv<df64>(const double*, const float2* rf, int i) {
+template <class T> LCDM_HD T recv(const double* rd, const float2* rf, int i);
+template <> LCDM_HD double recv<double>(const double* rd, const float2*, int i) { return rd[i]; }
+template <> LCDM_HD float recv<float>(const double*, const float2* rf, int i) { return rf[i].x; }
+template <> LCDM_HD df64 recv<df64>(const double*, const float2* rf, int i) {
     float2 v = rf[i];
     return mkdf(v.x, v.y);
 }
@@ -114,7 +114,7 @@ template <> __device__ __forceinline__ df64 recv<df64>(const double*, const floa
 template <class T, int K, bool WT, bool WX> struct PairEval {
     typedef typename std::conditional<(K > 0), Dual<T, K>, T>::type S;
 
-    static __device__ __forceinline__ S val(const double* rd, const float2* rf, int i, int di) {
+    static LCDM_HD S val(const double* rd, const float2* rf, int i, int di) {
         S s;
         if constexpr (K > 0) {
             s.v = recv<T>(rd, rf, i);
@@ -126,7 +126,7 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
         return s;
     }
     // Y = sqrt(-r) with its tangent -dr / (2Y)
-    static __device__ __forceinline__ S yval(const double* rd, const float2* rf, int iy, const S& r) {
+    static LCDM_HD S yval(const double* rd, const float2* rf, int iy, const S& r) {
         S y;
         if constexpr (K > 0) {
             y.v = recv<T>(rd, rf, iy);
@@ -139,7 +139,7 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
         return y;
     }
 
-    static __device__ __forceinline__ void run(T z, const double* rd, const float2* rf, int kind, S& Ichi,
+    static LCDM_HD void run(T z, const double* rd, const float2* rf, int kind, S& Ichi,
                                                S& It, S& IX, int* fail) {
         S A = val(rd, rf, RF_A, RF_DA);
         S amh = val(rd, rf, RF_AMH, RF_DAMH);
@@ -190,9 +190,9 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
     }
 };
 
-__device__ __forceinline__ float to_io(float v, float) { return v; }
-__device__ __forceinline__ double to_io(double v, double) { return v; }
-__device__ __forceinline__ float to_io(df64 v, float) { return v.hi + v.lo; }
+LCDM_HD float to_io(float v, float) { return v; }
+LCDM_HD double to_io(double v, double) { return v; }
+LCDM_HD float to_io(df64 v, float) { return v.hi + v.lo; }
 
 // per-pair results in the output type TO
 template <class TO, int K> struct PairOut {
@@ -205,10 +205,10 @@ template <class TO> __device__ __forceinline__ TO load_io(const void* p, int64_t
     return __ldg(reinterpret_cast<const TO*>(p) + i);
 }
 
-// Evaluate one pair.  PREC 0: FP64 throughout.  PREC 1: FP32, with a double-
-// float island whenever X or a tangent of t is requested.
+// Evaluate one pair.  PREC 0: FP64 throughout.  PREC 1: FP32 throughout (the
+// root records come from the FP64 preparation).
 template <int PREC, int K, bool WT, bool WX>
-__device__ __forceinline__ void eval_pair(typename std::conditional<PREC == 0, double, float>::type zin,
+LCDM_HD void eval_pair(typename std::conditional<PREC == 0, double, float>::type zin,
                                           const double* rd, const float2* rf, PairOut<
                                           typename std::conditional<PREC == 0, double, float>::type, K>& o,
                                           int* fail) {
@@ -216,41 +216,19 @@ __device__ __forceinline__ void eval_pair(typename std::conditional<PREC == 0, d
     const int kind = (int)rf[RF_KIND].x;
     TO Ichi, It = 0, IX = 0;
     TO dIchi[K > 0 ? K : 1], dIt[K > 0 ? K : 1], dIX[K > 0 ? K : 1];
-    const bool island = PREC == 1 && (WX || (WT && K > 0));
-    if constexpr (PREC == 0) {
-        typedef PairEval<double, K, WT, WX> E;
+    {
+        typedef PairEval<TO, K, WT, WX> E;
         typename E::S a, b, c;
         E::run(zin, rd, rf, kind, a, b, c, fail);
         if constexpr (K > 0) {
-            Ichi = a.v; It = b.v; IX = c.v;
-            for (int k = 0; k < K; k++) { dIchi[k] = a.d[k]; dIt[k] = b.d[k]; dIX[k] = c.d[k]; }
-        } else {
-            Ichi = a; It = WT ? b : 0.0; IX = WX ? c : 0.0;
-        }
-    } else if (island) {
-        // one double-float variant per tangent count: t and X are both evaluated
-        typedef PairEval<df64, K, true, true> E;
-        typename E::S a, b, c;
-        E::run(mkdf(zin), rd, rf, kind, a, b, c, fail);
-        if constexpr (K > 0) {
-            Ichi = to_io(a.v, 0.f); It = to_io(b.v, 0.f); IX = to_io(c.v, 0.f);
+            Ichi = a.v; It = WT ? b.v : (TO)0; IX = WX ? c.v : (TO)0;
             for (int k = 0; k < K; k++) {
-                dIchi[k] = to_io(a.d[k], 0.f);
-                dIt[k] = to_io(b.d[k], 0.f);
-                dIX[k] = to_io(c.d[k], 0.f);
+                dIchi[k] = a.d[k];
+                dIt[k] = WT ? b.d[k] : (TO)0;
+                dIX[k] = WX ? c.d[k] : (TO)0;
             }
         } else {
-            Ichi = to_io(a, 0.f); It = to_io(b, 0.f); IX = to_io(c, 0.f);
-        }
-    } else {
-        typedef PairEval<float, K, WT, false> E;
-        typename E::S a, b, c;
-        E::run(zin, rd, rf, kind, a, b, c, fail);
-        if constexpr (K > 0) {
-            Ichi = a.v;
-            for (int k = 0; k < K; k++) dIchi[k] = a.d[k];
-        } else {
-            Ichi = a; It = WT ? b : 0.f;
+            Ichi = a; It = WT ? b : (TO)0; IX = WX ? c : (TO)0;
         }
     }
     // observables

@@ -1,26 +1,45 @@
 // Device arithmetic for the Carlson-integral distance path.
 //
 //  * df64        double-float numbers (an unevaluated sum of two floats,
-//                Dekker/Knuth error-free transformations).  On GB300 the FP64
-//                pipe issues about 1.6 DFMA per SM per clock against about
-//                115 FFMA, so the high-precision island of the mixed path is
-//                built on FP32 pairs instead of FP64.
+//                Dekker/Knuth error-free transformations), used for the
+//                per-lane accumulators of the reductions (GB300 issues about
+//                1.6 DFMA per SM per clock against about 115 FFMA).
 //  * Dual<T,K>   value + K tangents (forward mode over the density parameters).
 //  * Cx<S>       complex numbers over any scalar S.
 //  * CPair/RPair the two roots (or integral arguments) that are either a complex
 //                conjugate pair or two reals, with the operations the formulas
 //                need (sum and product of the members are real in both cases).
 //  * carlson_dup one duplication sequence on (x1, x2, x3) shared by R_F, the
-//                three R_D with each argument in turn as the special one, and up
-//                to two R_J tracks (eqs. 2.6-2.9), after Carlson's duplication
-//                algorithm (the paper's ref. [10]).
+//                three R_D with each argument in turn as the special one, up to
+//                two R_J tracks (eqs. 2.6-2.9), after Carlson's duplication
+//                algorithm (the paper's ref. [10]), and optionally the divided
+//                difference of the last R_J track against R_D; generic over
+//                plain and dual numbers.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+// Function qualifiers (overridable: the arithmetic is plain C++ and also
+// compiles for the host).
+#ifndef LCDM_HD
 #define LCDM_HD __device__ __forceinline__
+#endif
 // heavy routines are real calls: each instantiation is optimised once
+#ifndef LCDM_NI
 #define LCDM_NI __device__ __noinline__
+#endif
+// round-to-nearest float add / sub / mul that the compiler may not contract
+#ifdef __CUDA_ARCH__
+#define LCDM_FADD(a, b) __fadd_rn(a, b)
+#define LCDM_FSUB(a, b) __fsub_rn(a, b)
+#define LCDM_FMUL(a, b) __fmul_rn(a, b)
+#define LCDM_FDIV(a, b) __fdiv_rn(a, b)
+#else
+#define LCDM_FADD(a, b) ((a) + (b))
+#define LCDM_FSUB(a, b) ((a) - (b))
+#define LCDM_FMUL(a, b) ((a) * (b))
+#define LCDM_FDIV(a, b) ((a) / (b))
+#endif
 
 namespace lcdm {
 
@@ -35,42 +54,42 @@ LCDM_HD df64 df_from_double(double d) { float h = (float)d; return mkdf(h, (floa
 LCDM_HD double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
 // error-free sum (Knuth), sum with |a| >= |b| (Dekker), product via FMA
 LCDM_HD df64 two_sum(float a, float b) {
-    float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
-    float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    float s = LCDM_FADD(a, b), bb = LCDM_FSUB(s, a);
+    float e = LCDM_FADD(LCDM_FSUB(a, LCDM_FSUB(s, bb)), LCDM_FSUB(b, bb));
     return mkdf(s, e);
 }
 LCDM_HD df64 fast_two_sum(float a, float b) {
-    float s = __fadd_rn(a, b);
-    return mkdf(s, __fsub_rn(b, __fsub_rn(s, a)));
+    float s = LCDM_FADD(a, b);
+    return mkdf(s, LCDM_FSUB(b, LCDM_FSUB(s, a)));
 }
 LCDM_HD df64 operator+(df64 a, df64 b) {
     df64 s = two_sum(a.hi, b.hi), t = two_sum(a.lo, b.lo);
-    s.lo = __fadd_rn(s.lo, t.hi);
+    s.lo = LCDM_FADD(s.lo, t.hi);
     s = fast_two_sum(s.hi, s.lo);
-    s.lo = __fadd_rn(s.lo, t.lo);
+    s.lo = LCDM_FADD(s.lo, t.lo);
     return fast_two_sum(s.hi, s.lo);
 }
 LCDM_HD df64 operator-(df64 a) { return mkdf(-a.hi, -a.lo); }
 LCDM_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
 LCDM_HD df64 operator*(df64 a, df64 b) {
-    float p = __fmul_rn(a.hi, b.hi);
+    float p = LCDM_FMUL(a.hi, b.hi);
     float e = fmaf(a.hi, b.hi, -p);
     e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
     return fast_two_sum(p, e);
 }
 LCDM_HD df64 operator/(df64 a, df64 b) {
-    float q1 = __fdiv_rn(a.hi, b.hi);
+    float q1 = LCDM_FDIV(a.hi, b.hi);
     df64 r = a - b * mkdf(q1);
-    float q2 = __fdiv_rn(r.hi, b.hi);
+    float q2 = LCDM_FDIV(r.hi, b.hi);
     r = r - b * mkdf(q2);
-    float q3 = __fdiv_rn(r.hi, b.hi);
+    float q3 = LCDM_FDIV(r.hi, b.hi);
     df64 q = fast_two_sum(q1, q2);
     return q + mkdf(q3);
 }
 LCDM_HD df64 operator+(df64 a, float b) { return a + mkdf(b); }
 LCDM_HD df64 operator-(df64 a, float b) { return a - mkdf(b); }
 LCDM_HD df64 operator*(df64 a, float b) {
-    float p = __fmul_rn(a.hi, b);
+    float p = LCDM_FMUL(a.hi, b);
     float e = fmaf(a.hi, b, -p);
     e = fmaf(a.lo, b, e);
     return fast_two_sum(p, e);
@@ -81,10 +100,10 @@ LCDM_HD df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
 LCDM_HD df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
 // square root by one Newton-type correction of the float estimate (Karp)
 LCDM_HD df64 df_sqrt(df64 a) {
-    if (!(a.hi > 0.f)) return mkdf(a.hi == 0.f ? 0.f : __int_as_float(0x7fc00000));
+    if (!(a.hi > 0.f)) return mkdf(a.hi == 0.f ? 0.f : nanf(""));
     float x = 1.0f / sqrtf(a.hi);
-    float y = __fmul_rn(a.hi, x);
-    float p = __fmul_rn(y, y);
+    float y = LCDM_FMUL(a.hi, x);
+    float p = LCDM_FMUL(y, y);
     df64 r = a - mkdf(p, fmaf(y, y, -p));
     return fast_two_sum(y, r.hi * (0.5f * x));
 }
@@ -101,10 +120,11 @@ LCDM_HD df64 ssqrt(df64 a) { return df_sqrt(a); }
 LCDM_HD float sabs(float a) { return fabsf(a); }
 LCDM_HD double sabs(double a) { return fabs(a); }
 LCDM_HD df64 sabs(df64 a) { return a.hi < 0.f ? -a : a; }
-template <class T> LCDM_HD T cst(double v);
-template <> LCDM_HD float cst<float>(double v) { return (float)v; }
-template <> LCDM_HD double cst<double>(double v) { return v; }
-template <> LCDM_HD df64 cst<df64>(double v) { return df_from_double(v); }
+template <class T> struct CstImpl;
+template <> struct CstImpl<float> { static LCDM_HD float make(double v) { return (float)v; } };
+template <> struct CstImpl<double> { static LCDM_HD double make(double v) { return v; } };
+template <> struct CstImpl<df64> { static LCDM_HD df64 make(double v) { return df_from_double(v); } };
+template <class T> LCDM_HD T cst(double v) { return CstImpl<T>::make(v); }
 // exact multiplication by 2^e
 LCDM_HD float sldexp(float a, int e) { return ldexpf(a, e); }
 LCDM_HD double sldexp(double a, int e) { return ldexp(a, e); }
@@ -186,6 +206,15 @@ template <class T, int K> LCDM_HD Dual<T, K> dlin(T v, T g, const Dual<T, K>& x)
 template <class T, int K> LCDM_HD void dacc(Dual<T, K>& r, T g, const Dual<T, K>& x) {
 #pragma unroll
     for (int k = 0; k < K; k++) r.d[k] = r.d[k] + g * x.d[k];
+}
+template <class T, int K> struct CstImpl<Dual<T, K> > {
+    static LCDM_HD Dual<T, K> make(double v) { return dconst<T, K>(CstImpl<T>::make(v)); }
+};
+template <class T, int K> LCDM_HD Dual<T, K> sldexp(const Dual<T, K>& a, int e) {
+    Dual<T, K> r; r.v = sldexp(a.v, e);
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = sldexp(a.d[k], e);
+    return r;
 }
 // base scalar of a (possibly dual) scalar, and constants of that base type
 template <class S> struct Base { typedef S type; };
@@ -342,6 +371,13 @@ template <> struct Prec<df64> {
     enum { rc_terms = 12, maxit = 40 };
 };
 
+// dual numbers follow the precision of their base type
+template <class T, int K> struct Prec<Dual<T, K> > {
+    static LCDM_HD Dual<T, K> tol() { return dconst<T, K>(Prec<T>::tol()); }
+    static LCDM_HD Dual<T, K> rc_series_max() { return dconst<T, K>(Prec<T>::rc_series_max()); }
+    enum { rc_terms = Prec<T>::rc_terms, maxit = Prec<T>::maxit };
+};
+
 // R_C(x, y) = R_F(x, y, y) (eq. 2.8) by duplication; value only.
 template <class T> LCDM_HD T rc_value(T x, T y, int* fail) {
     const T tol = Prec<T>::tol();
@@ -378,6 +414,18 @@ template <class T> LCDM_HD T rc1(T e, int* fail) {
     return rc_value(cst<T>(1.0), cst<T>(1.0) + e, fail);
 }
 
+// (R_C(1, 1+e) - 1) / e = sum_{n>=1} (-e)^n / (2n+1) / e, without cancellation.
+template <class T> LCDM_HD T rc1_minus1_over_e(T e, int* fail) {
+    if (sval(sabs(e)) <= sval(Prec<T>::rc_series_max())) {
+        T w = -e;
+        T s = cst<T>(-1.0 / (2 * Prec<T>::rc_terms + 3));
+#pragma unroll
+        for (int n = Prec<T>::rc_terms; n >= 1; n--) s = cst<T>(-1.0 / (2 * n + 1)) + w * s;
+        return s;
+    }
+    return (rc_value(cst<T>(1.0), cst<T>(1.0) + e, fail) - cst<T>(1.0)) / e;
+}
+
 // Series of R_J (and of R_D = R_J with p equal to one argument) in the
 // normalised deviations: X for the single argument, sumY / prodY for the pair,
 // P for p.  U is a scalar or a complex type.
@@ -397,12 +445,29 @@ template <class T> LCDM_HD Cx<T> operator+(const Cx<T>& a, const T& s) { return 
 template <class T> LCDM_HD Cx<T> operator-(const T& s, const Cx<T>& a) { return mkcx<T>(s - a.re, -a.im); }
 template <class T> LCDM_HD Cx<T> operator-(const Cx<T>& a, const T& s) { return mkcx<T>(a.re - s, a.im); }
 
+// Divided-difference numbers: the values of a quantity at two points u1, u2
+// and its divided difference (v1 - v2) / (u1 - u2), with the product rule
+// [fg] = [f] g(u1) + f(u2) [g].  Used to evaluate R_J(p) - R_J(p') for close
+// p, p' without cancellation.
+template <class T> struct DD { T v1, v2, d; };
+template <class T> LCDM_HD DD<T> mkdd(T a, T b, T d) { DD<T> r; r.v1 = a; r.v2 = b; r.d = d; return r; }
+template <class T> LCDM_HD DD<T> operator+(const DD<T>& a, const DD<T>& b) { return mkdd<T>(a.v1 + b.v1, a.v2 + b.v2, a.d + b.d); }
+template <class T> LCDM_HD DD<T> operator-(const DD<T>& a, const DD<T>& b) { return mkdd<T>(a.v1 - b.v1, a.v2 - b.v2, a.d - b.d); }
+template <class T> LCDM_HD DD<T> operator*(const DD<T>& a, const DD<T>& b) {
+    return mkdd<T>(a.v1 * b.v1, a.v2 * b.v2, a.d * b.v1 + a.v2 * b.d);
+}
+template <class T> LCDM_HD DD<T> operator*(const DD<T>& a, const T& c) { return mkdd<T>(a.v1 * c, a.v2 * c, a.d * c); }
+template <class T> LCDM_HD DD<T> operator+(const DD<T>& a, const T& c) { return mkdd<T>(a.v1 + c, a.v2 + c, a.d); }
+template <class T> LCDM_HD DD<T> operator-(const T& c, const DD<T>& a) { return mkdd<T>(c - a.v1, c - a.v2, -a.d); }
+template <class T> LCDM_HD DD<T> operator-(const DD<T>& a, const T& c) { return mkdd<T>(a.v1 - c, a.v2 - c, a.d); }
+
 template <class T, int NJ, class PT>
 struct DupResult {
     T RF;      // R_F(x1, x2, x3)
     T RD1;     // R_D(x2, x3, x1): x1 special
-    PT RDp;    // R_D(x1, x3, x2), R_D(x1, x2, x3): pair member special
+    PT RDp;    // R_D(x1, x2, x3), R_D(x1, x2, x3): pair member special
     T RJ[NJ];  // R_J(x1, x2, x3, p_j)
+    T DJ;      // (R_J(x1,x2,x3,p_last) - R_D(x2,x3,x1)) / (p_last - x1)  (when requested)
 };
 
 // R_D with a pair member special, from the final duplicated arguments.
@@ -442,8 +507,11 @@ LCDM_HD int even_exponent(float mag) {
 // One duplication sequence for R_F, R_D (all three specials when WANT_D) and
 // NJ R_J tracks with p_j > 0.  The triple is (x1, pair).  Arguments are first
 // scaled by an even power of two (exact; R_F ~ s^-1/2, R_D and R_J ~ s^-3/2).
-template <class T, int NJ, bool WANT_D, class PT>
-LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail) {
+// With DDL, the last track is p = x1 + hl (hl given separately, exactly) and
+// DJ = (R_J(p) - R_D(x2, x3, x1)) / hl is evaluated term by term (sum terms
+// and the final series) so that close p and x1 cause no cancellation.
+template <class T, int NJ, bool WANT_D, class PT, bool DDL = false>
+LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T hl = T()) {
     DupResult<T, NJ, PT> R;
     float mag = fabsf((float)sval(x1));
     float pm = pmag(pr);
@@ -468,6 +536,12 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail) {
     T sD1 = cst<T>(0.0);
     PT sDp = pzero(pr);
     T f = cst<T>(1.0);
+    // divided-difference track: h = p_last - x1 (scaled), Pi = prod(p_last - pair)
+    T hs = cst<T>(0.0), sDD = cst<T>(0.0), PiL = cst<T>(0.0);
+    if (DDL) {
+        hs = sldexp(hl, -e);
+        PiL = pprod(prsub(p[NJ - 1], pr));
+    }
     const T tol = Prec<T>::tol();
     int m = 0;
     for (; m < Prec<T>::maxit; m++) {
@@ -499,6 +573,16 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail) {
             T f3 = f * f * f;
             T ee = f3 * delta[j] / (d * d);
             sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
+            if (DDL && j == NJ - 1) {
+                // [R_C(1,1+e)/d_p - 1/d_x1] / h with e/h = f^3 Pi / d_p^2 and
+                // (d_p - d_x1)/h = f [g(a) + 2b (a + b + sum sqrt(pair))] / (a + b),
+                // a = sqrt(p), b = sqrt(x1), g(v) = prod(v + sqrt(pair)), d_x1 = 2 b g(b)
+                T eh = f3 * PiL / (d * d);
+                T F1 = rc1_minus1_over_e(ee, fail);
+                T dx1 = cst<T>(2.0) * s1 * pprod(padd(sp, s1));
+                T ddp = f * (pprod(padd(sp, sq)) + cst<T>(2.0) * s1 * (sq + s1 + psum(sp))) / (sq + s1);
+                sDD = sDD + f * (eh * F1 / d - ddp / (d * dx1));
+            }
         }
         x1 = (x1 + lam) * cst<T>(0.25);
         pr = pscale(padd(pr, lam), cst<T>(0.25));
@@ -532,6 +616,30 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail) {
         PT Y = pscale(prsub(A, pr), iA);
         T ser = rj_series<T, T>(X, psum(Y), pprod(Y), P);
         R.RJ[j] = sldexp(f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j], -3 * e / 2);
+    }
+    if (DDL) {
+        // final series: A(u) = (sig + 2u)/5 at u1 = p, u2 = x1; X = 1 - x1/A,
+        // Y = 1 - pair/A, P = 1 - u/A; divided differences by the product rule
+        const T sig = x1 + psum(pr);
+        const T u1 = x1 + hs * f;   // p after m steps (p - x1 shrinks by 4 each step)
+        T A1 = (sig + cst<T>(2.0) * u1) * cst<T>(0.2), A2 = (sig + cst<T>(2.0) * x1) * cst<T>(0.2);
+        T iA1 = cst<T>(1.0) / A1, iA2 = cst<T>(1.0) / A2;
+        T dInv = cst<T>(-0.4) * iA1 * iA2;                 // [1/A]
+        DD<T> inv = mkdd<T>(iA1, iA2, dInv);
+        DD<T> X = cst<T>(1.0) - inv * x1;
+        DD<T> sY = cst<T>(2.0) - inv * psum(pr);
+        DD<T> inv2 = inv * inv;
+        DD<T> pY = (cst<T>(1.0) - inv * psum(pr)) + inv2 * pprod(pr);
+        DD<T> P = mkdd<T>(cst<T>(1.0) - u1 * iA1, cst<T>(1.0) - x1 * iA2, sig * cst<T>(-0.2) * iA1 * iA2);
+        DD<T> ser = rj_series<DD<T>, T>(X, sY, pY, P);
+        // [A^-3/2] = -(2/5)(A1 + sqrt(A1 A2) + A2) / ((sqrt A1 + sqrt A2) A1^3/2 A2^3/2)
+        T r1 = ssqrt(A1), r2 = ssqrt(A2);
+        T a32_1 = iA1 / r1, a32_2 = iA2 / r2;
+        T dA32 = cst<T>(-0.4) * (A1 + r1 * r2 + A2) / (r1 + r2) * a32_1 * a32_2;
+        T dser = dA32 * ser.v1 + a32_2 * ser.d;          // [A^-3/2 S]
+        // R_J(p) - R_D = f (T(u1) - T(u2)) + 6 (sum_p - sum_x1), T = A^-3/2 S,
+        // with u1 - u2 = f hs and the sums' difference = hs sDD
+        R.DJ = sldexp(f * f * dser + cst<T>(6.0) * sDD, -5 * e / 2);
     }
     return R;
 }

@@ -8,17 +8,17 @@ namespace lcdm {
 
 // ---------------------------------------------------------------- roots -----
 struct cd { double re, im; };
-__device__ __forceinline__ cd cmk(double r, double i) { cd c; c.re = r; c.im = i; return c; }
-__device__ __forceinline__ cd cadd(cd a, cd b) { return cmk(a.re + b.re, a.im + b.im); }
-__device__ __forceinline__ cd csub(cd a, cd b) { return cmk(a.re - b.re, a.im - b.im); }
-__device__ __forceinline__ cd cmul(cd a, cd b) { return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
-__device__ __forceinline__ cd cdiv(cd a, cd b) {
+LCDM_HD cd cmk(double r, double i) { cd c; c.re = r; c.im = i; return c; }
+LCDM_HD cd cadd(cd a, cd b) { return cmk(a.re + b.re, a.im + b.im); }
+LCDM_HD cd csub(cd a, cd b) { return cmk(a.re - b.re, a.im - b.im); }
+LCDM_HD cd cmul(cd a, cd b) { return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+LCDM_HD cd cdiv(cd a, cd b) {
     double s = fabs(b.re) > fabs(b.im) ? fabs(b.re) : fabs(b.im);
     double br = b.re / s, bi = b.im / s, n = br * br + bi * bi;
     return cmk((a.re * br + a.im * bi) / (s * n), (a.im * br - a.re * bi) / (s * n));
 }
-__device__ __forceinline__ double cabs_(cd a) { return hypot(a.re, a.im); }
-__device__ __forceinline__ cd csqrt_(cd a) {
+LCDM_HD double cabs_(cd a) { return hypot(a.re, a.im); }
+LCDM_HD cd csqrt_(cd a) {
     double r = cabs_(a);
     if (a.re >= 0) { double t = sqrt(0.5 * (r + a.re)); return cmk(t, t > 0 ? a.im / (2 * t) : 0.0); }
     double t = sqrt(0.5 * (r - a.re));
@@ -26,7 +26,7 @@ __device__ __forceinline__ cd csqrt_(cd a) {
 }
 
 // p(x) = sum_k c[k] x^k (degree n, c[n] = 1) and p'(x) by Horner's rule
-__device__ __forceinline__ void horner(const double* c, int n, cd x, cd& p, cd& dp) {
+LCDM_HD void horner(const double* c, int n, cd x, cd& p, cd& dp) {
     p = cmk(c[n], 0); dp = cmk(0, 0);
     for (int k = n - 1; k >= 0; k--) { dp = cadd(cmul(dp, x), p); p = cadd(cmul(p, x), cmk(c[k], 0)); }
 }
@@ -34,7 +34,7 @@ __device__ __forceinline__ void horner(const double* c, int n, cd x, cd& p, cd& 
 // Roots of the monic polynomial c (degree n <= 4) by the Aberth-Ehrlich
 // iteration started on circles whose radii come from the Newton polygon of
 // log|c_k| (so a root near -Om/Or and the O(1) roots both start close).
-__device__ int poly_roots(const double* c, int n, cd* z) {
+LCDM_HD int poly_roots(const double* c, int n, cd* z) {
     // upper convex hull of (k, log|c_k|)
     double lg[5];
     int idx[5], m = 0;
@@ -90,7 +90,7 @@ __device__ int poly_roots(const double* c, int n, cd* z) {
     return it;
 }
 
-__device__ __forceinline__ void polish_real(const double* c, int n, double& x) {
+LCDM_HD void polish_real(const double* c, int n, double& x) {
     for (int k = 0; k < 3; k++) {
         double p = c[n], dp = 0;
         for (int j = n - 1; j >= 0; j--) { dp = dp * x + p; p = p * x + c[j]; }
@@ -101,17 +101,11 @@ __device__ __forceinline__ void polish_real(const double* c, int n, double& x) {
     }
 }
 
-// One thread per cosmology.  params [B][ncol] = (H0, Om, OL, Or[, Ok]).
-// grad / loglike (optional): rows initialised to 0 (NaN for a bad status).
-__global__ void prep_kernel(const double* __restrict__ params, int64_t B, int ncol, double* __restrict__ recD,
-                            float2* __restrict__ recF, int32_t* __restrict__ status, double* __restrict__ grad,
-                            double* __restrict__ loglike) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
-    const double* p = params + b * ncol;
+// Record of one cosmology from its parameter row p[ncol] = (H0, Om, OL, Or[, Ok]);
+// returns the status code.
+LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
     double H0 = p[0], Om = p[1], OL = p[2], Or = p[3];
     double Ok = ncol >= 5 ? p[4] : 1.0 - Om - OL - Or;
-    double rec[NREC];
     for (int i = 0; i < NREC; i++) rec[i] = 0;
     int st = ST_OK, kind = 0;
     const int K = ncol - 1;
@@ -197,7 +191,7 @@ __global__ void prep_kernel(const double* __restrict__ params, int64_t B, int nc
                     }
                     dr[j][k] = cmk(0, 0);
                     if (den.re != 0 || den.im != 0) dr[j][k] = cdiv(cmk(-s.re, -s.im), den);
-                    if (n == 3 && k == 2) dr[j][k] = cmk(CUDART_NAN, CUDART_NAN);  // no Or direction in a cubic
+                    if (n == 3 && k == 2) dr[j][k] = cmk(nan(""), nan(""));  // no Or direction in a cubic
                 }
             }
             // big-root quantities of the quartic, scaled by lam = Or (see quartic_integrals)
@@ -238,9 +232,21 @@ __global__ void prep_kernel(const double* __restrict__ params, int64_t B, int nc
         rec[RF_DAMH + k] = 0;
         if (n == 4 && k == 2) rec[RF_DAMH + k] = -0.5 * amh / Or;
         if (n == 3 && k == 0) rec[RF_DAMH + k] = -0.5 * amh / Om;
-        if (n == 3 && k == 2) rec[RF_DAMH + k] = CUDART_NAN;
+        if (n == 3 && k == 2) rec[RF_DAMH + k] = nan("");
         rec[RF_DOK + k] = ncol == 4 ? -1.0 : (k == 3 ? 1.0 : 0.0);
     }
+    return st;
+}
+
+// One thread per cosmology.  grad / loglike (optional): rows initialised to 0
+// (NaN for a bad status).
+__global__ void prep_kernel(const double* __restrict__ params, int64_t B, int ncol, double* __restrict__ recD,
+                            float2* __restrict__ recF, int32_t* __restrict__ status, double* __restrict__ grad,
+                            double* __restrict__ loglike) {
+    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= B) return;
+    double rec[NREC];
+    int st = prep_one(params + b * ncol, ncol, rec);
     double* rd = recD + b * NREC;
     float2* rf = recF + b * NREC;
     for (int i = 0; i < NREC; i++) {
@@ -249,7 +255,7 @@ __global__ void prep_kernel(const double* __restrict__ params, int64_t B, int nc
         rf[i] = make_float2(h, (float)(rec[i] - (double)h));
     }
     status[b] = st;
-    double init = st == ST_OK ? 0.0 : CUDART_NAN;
+    double init = st == ST_OK ? 0.0 : nan("");
     if (grad)
         for (int k = 0; k < ncol; k++) grad[b * ncol + k] = init;
     if (loglike) loglike[b] = init;

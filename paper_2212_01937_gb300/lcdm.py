@@ -6,8 +6,8 @@ is no fallback: if the library is missing, :func:`load` raises.
 
 Layouts (see include/lcdm.h): ``"csr"`` (offsets [B+1] int64, z [nnz]),
 ``"dense"`` (z [B*n], n per row) and ``"shared"`` (z [n] shared by all rows).
-Precision ``"fp32"`` (LCDM_FP32_MIXED: float32 I/O, FP64 roots and
-reductions, double-float island for X and the tangent of t) or ``"fp64"``.
+Precision ``"fp32"`` (LCDM_FP32_MIXED: float32 I/O and per-pair arithmetic,
+FP64 root preparation and reductions) or ``"fp64"``.
 """
 import ctypes
 import os
