@@ -146,8 +146,8 @@ lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* o
 /* Times the candidate launch shapes (threads per block x persistent blocks
  * per SM) of the pair kernel on the given inputs, keeps the fastest in a
  * process-wide cache keyed by (precision, outputs, tangents, layout, log2
- * npairs) and returns it.  Arguments as lcdm_distances_vjp (cot and grad may
- * be NULL for a forward-only shape; out entries are overwritten).  The call
+ * npairs) and returns it.  Arguments as lcdm_distances_vjp (grad NULL selects
+ * a forward-only shape and cot is then ignored; out entries are overwritten).  The call
  * synchronises the stream; do not call it while capturing a CUDA graph.    */
 lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
                           const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT], double* grad,

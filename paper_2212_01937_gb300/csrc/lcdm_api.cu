@@ -276,7 +276,7 @@ lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offset
                           cudaStream_t stream, int32_t* best_block, int32_t* best_bps, float* best_ms) {
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
-    if ((cot == nullptr) != (grad == nullptr)) return LCDM_ERR_INVALID;
+    if (!grad) cot = nullptr;   // forward-only shape
     Carved cv;
     st = carve(ws, ws_bytes, B, cv);
     if (st != LCDM_OK) return st;
