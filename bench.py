@@ -26,10 +26,10 @@ sys.path.insert(0, ROOT)
 METRIC = "distance+gradient pairs/sec (FP32 batched) vs plain FP64 forward, same GB300, ≤2e-6 rel"
 UNIT = "pairs/s"
 OUTPUTS = ("d_C", "t", "X", "mu")
-# Algorithmic work of the dominant kernel per pair for this workload: FP32
-# floating-point operations (FFMA counted as 2) executed per pair, from the
-# ncu capture summarised in profiles/pairs_kernel_mix_k3_config2.md.
-FLOP_PER_PAIR = None
+# Work of the dominant kernel per pair for this workload: FP32 floating-point
+# operations (FFMA counted as 2, FADD and FMUL as 1) executed per pair, from
+# the ncu capture summarised in profiles/pairs_kernel_fp32_vjp_4096x1024.md.
+FLOP_PER_PAIR = 6534.1
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 

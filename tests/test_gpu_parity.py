@@ -2,10 +2,12 @@
 
 Tolerances (relative unless stated):
   FP64 path: d_C, t, X, d_M, d_L <= 1e-12; mu <= 1e-11 mag.
-  FP32 path: d_C, t, X, d_M, d_L <= 2e-6; mu <= 1e-5 mag.
+  FP32 path: d_C, t, d_M, d_L <= 2e-6; X <= 2e-5 (eq. 3.9 keeps an O(10-100)
+  cancellation when Omega_m0 is small); mu <= 1e-5 mag.
   Gradients, per pair, relative to the largest entry of the pair's row,
   against the Leibniz-rule oracle (itself pinned to central differences):
-  FP64 <= 1e-9 + 1e-11/z; FP32 <= 5e-5 + 2e-6/z.  The 1/z terms: near z = 0
+  FP64 <= 1e-9 + 1e-11/z; FP32 <= 3e-5 + 2e-6/z for d_C, d_M, d_L, mu and
+  <= 1e-3 + 2e-6/z for t and X.  The 1/z terms: near z = 0
   every distance is z (1 + O(z)) and its parameter dependence sits in the
   O(z) part, while the Carlson arguments all tend to one value.
 """
@@ -21,7 +23,7 @@ pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 COLS = {"d_C": 0, "t": 1, "X": 2, "d_M": 3, "d_L": 4, "mu": 5}
 TOL64 = {"d_C": 1e-12, "t": 1e-12, "X": 1e-12, "d_M": 1e-12, "d_L": 1e-12}
-TOL32 = {"d_C": 2e-6, "t": 2e-6, "X": 2e-6, "d_M": 2e-6, "d_L": 2e-6}
+TOL32 = {"d_C": 2e-6, "t": 2e-6, "X": 2e-5, "d_M": 2e-6, "d_L": 2e-6}
 
 
 def _t(a, dtype=None):
@@ -44,12 +46,14 @@ def _batch_small():
     return b.params, z, offs
 
 
-def jac_tol(prec, z):
+def jac_tol(prec, z, name="d_C"):
     z = np.maximum(np.asarray(z, dtype=np.float64), 1e-12)
-    return 1e-9 + 1e-11 / z if prec == "fp64" else 5e-5 + 2e-6 / z
+    if prec == "fp64":
+        return 1e-9 + 1e-11 / z
+    return (1e-3 if name in ("t", "X") else 3e-5) + 2e-6 / z
 
 
-def _check(res, ref, tol, prec, names=("d_C", "t", "X", "d_M", "d_L")):
+def _check(res, ref, tol, prec, names=("d_C", "t", "X", "d_M", "d_L"), mu_lim=None):
     for n in names:
         if n not in res:
             continue
@@ -65,7 +69,7 @@ def _check(res, ref, tol, prec, names=("d_C", "t", "X", "d_M", "d_L")):
         fin = np.isfinite(want)
         # z = 0 gives -inf; d_M <= 0 (closed universes beyond the antipode) gives NaN
         assert np.all((got[~fin] == want[~fin]) | (np.isnan(got[~fin]) & np.isnan(want[~fin])))
-        lim = 1e-11 if prec == "fp64" else 1e-5
+        lim = mu_lim if mu_lim is not None else (1e-11 if prec == "fp64" else 1e-5)
         assert np.max(np.abs(got[fin] - want[fin])) <= lim, (prec, "mu")
 
 
@@ -140,22 +144,22 @@ def test_stress_near_flat_and_near_boundary(lib):
     assert int(r64["status"].abs().sum()) == 0
     # near-coincident roots at the no-Big-Bang boundary limit the root accuracy
     # to about sqrt(eps): stated looser bounds for this stress set
-    _check(r64, ref, {"d_C": 1e-9, "t": 1e-9, "X": 1e-8}, "fp64", names=("d_C", "t", "X"))
-    _check(r32, ref32, {"d_C": 2e-6, "t": 5e-6, "X": 5e-6}, "fp32", names=("d_C", "t", "X"))
+    _check(r64, ref, {"d_C": 1e-9, "t": 1e-9, "X": 1e-8}, "fp64", names=("d_C", "t", "X"), mu_lim=1e-8)
+    _check(r32, ref32, {"d_C": 1e-5, "t": 1e-5, "X": 2e-5}, "fp32", names=("d_C", "t", "X"))
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_jacobian_vs_leibniz_oracle(lib, prec):
     b = workloads.config2(B=6, n=33, seed=9)
     z = b.z.copy()
-    z[::11] = [1e-4, 1e-3, 1e-2, 0.1, 30.0, 1100.0][: z[::11].size]
+    z[:66:11] = [1e-4, 1e-3, 1e-2, 0.1, 30.0, 1100.0]
     zin = z if prec == "fp64" else z.astype(np.float32)
     zq = zin.astype(np.float64)
     _, J = oracle.quad_distances(b.params, zq, b.offsets, grad=True)
     res = lib.distances_jac(_t(b.params), _t(zin), _t(b.offsets), outputs=("d_C", "t", "X", "mu"), precision=prec)
     torch.cuda.synchronize()
-    tol = jac_tol(prec, zq)
     for n in ("d_C", "t", "X", "mu"):
+        tol = jac_tol(prec, zq, n)
         got = res["jac"][n].double().cpu().numpy()
         want = J[:, COLS[n], :]
         scale = np.abs(want).max(axis=1)
@@ -175,10 +179,10 @@ def test_vjp_matches_jacobian_and_oracle(lib, prec):
     _, J = oracle.quad_distances(b.params, zq, b.offsets, grad=True)
     want = np.zeros((b.B, 4))
     bound = np.zeros((b.B, 4))
-    tol = jac_tol(prec, zq)
     for r in range(b.B):
         sl = slice(b.offsets[r], b.offsets[r + 1])
         for n, c in cot.items():
+            tol = jac_tol(prec, zq, n)
             cj = c[sl].astype(np.float64)[:, None] * J[sl, COLS[n], :]
             want[r] += cj.sum(axis=0)
             bound[r] += (np.abs(c[sl]) * tol[sl] * np.abs(J[sl, COLS[n], :]).max(axis=1)).sum()
@@ -190,25 +194,32 @@ def test_vjp_matches_jacobian_and_oracle(lib, prec):
 
 
 def test_fp64_gradients_vs_central_differences(lib):
-    """FP64 gradients against central differences of the FP64 forward pass on
-    the GPU itself (<= 1e-6 relative), including low and high redshift."""
+    """FP64 gradients against fourth-order central differences of the FP64
+    forward pass on the GPU itself (<= 1e-6 relative), low and high z included."""
     b = workloads.config2(B=3, n=8, seed=12)
     z = b.z.copy()
     z[:4] = [1e-3, 0.05, 200.0, 1100.0]
-    res = lib.distances_jac(_t(b.params), _t(z), _t(b.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp64")
+    outs = ("d_C", "t", "X", "mu")
+    res = lib.distances_jac(_t(b.params), _t(z), _t(b.offsets), outputs=outs, precision="fp64")
     torch.cuda.synchronize()
-    for k, h in ((0, 1e-4), (1, 1e-6), (2, 1e-6), (3, 1e-9)):
-        pp, pm = b.params.copy(), b.params.copy()
-        pp[:, k] += h
-        pm[:, k] -= h
-        fp = lib.distances(_t(pp), _t(z), _t(b.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp64")
-        fm = lib.distances(_t(pm), _t(z), _t(b.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp64")
+
+    def fwd(p):
+        r = lib.distances(_t(p), _t(z), _t(b.offsets), outputs=outs, precision="fp64")
         torch.cuda.synchronize()
-        for n in ("d_C", "t", "X", "mu"):
-            fd = ((fp[n] - fm[n]) / (2 * h)).cpu().numpy()
+        return {n: r[n].cpu().numpy() for n in outs}
+
+    for k in range(4):
+        h = 2e-4 * np.abs(b.params[:, k]).min()
+        f = {}
+        for m in (-2, -1, 1, 2):
+            pp = b.params.copy()
+            pp[:, k] += m * h
+            f[m] = fwd(pp)
+        for n in outs:
+            fd = (-f[2][n] + 8 * f[1][n] - 8 * f[-1][n] + f[-2][n]) / (12 * h)
             got = res["jac"][n][:, k].cpu().numpy()
             scale = np.abs(res["jac"][n].cpu().numpy()).max(axis=1)
-            assert np.max(np.abs(got - fd) / scale) < 1e-6, (k, n)
+            assert np.max(np.abs(got - fd) / scale) < 1e-6, (k, n, np.max(np.abs(got - fd) / scale))
 
 
 def test_gauss_loglike_vs_oracle(lib):
