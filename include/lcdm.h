@@ -143,6 +143,30 @@ lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* o
                                double* grad, void* mu_out, int32_t* cosmo_status, const lcdm_opts* opts,
                                void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Largest B accepted by lcdm_distances_static. */
+#define LCDM_STATIC_MAX_COSMOLOGIES 4096
+
+/* lcdm_distances without a workspace argument, for callers that cannot
+ * allocate device memory: for example a caller that is capturing a CUDA
+ * graph (where cudaMalloc is not allowed), one that runs under a fixed memory
+ * budget with no allocator of its own, or plain C code that has no device
+ * allocator at hand.  (The paper has no counterpart; this is a convenience of
+ * this library.)
+ *   Scratch lives in a fixed device array inside the library, sized for
+ *   LCDM_STATIC_MAX_COSMOLOGIES cosmologies (about 4 MB), which stays
+ *   allocated on every device that loads the library until the process exits.
+ *   B larger than that is rejected with LCDM_ERR_INVALID; nothing is enqueued.
+ *   The function calls no cudaMalloc, cudaFree or other allocating routine.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress); make that first call outside any stream capture.
+ *   Every call on a device shares the one array and overwrites it fully, so
+ *   calls whose kernels may overlap on the GPU (other streams, other host
+ *   threads) race: order them on one stream or serialise them.
+ *   Other arguments, outputs and status codes as lcdm_distances.           */
+lcdm_status lcdm_distances_static(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                  int64_t n, void* const out[LCDM_NOUT], int32_t* cosmo_status,
+                                  const lcdm_opts* opts, cudaStream_t stream);
+
 /* Times the candidate launch shapes (threads per block x persistent blocks
  * per SM) of the pair kernel on the given inputs, keeps the fastest in a
  * process-wide cache keyed by (precision, outputs, tangents, layout, log2

@@ -212,9 +212,51 @@ lcdm_status pairs_common(const double* params, int64_t B, const int64_t* offsets
     return launch_plan(P, opts->block, opts->blocks_per_sm, stream);
 }
 
+// ----------------------------------------------------------------------------
+// Fixed device scratch for lcdm_distances_static.  The array belongs to this
+// translation unit; its device address is looked up once per device with
+// cudaGetSymbolAddress (the host-side name is only a stand-in and must never
+// be handed to a kernel).
+// ----------------------------------------------------------------------------
+#define LCDM_STATIC_WS_BYTES (((size_t)LCDM_STATIC_MAX_COSMOLOGIES * NREC * sizeof(double) + 255) / 256 * 256 + \
+                              ((size_t)LCDM_STATIC_MAX_COSMOLOGIES * NREC * sizeof(float2) + 255) / 256 * 256)
+static __device__ __align__(256) unsigned char g_static_ws[LCDM_STATIC_WS_BYTES];
+
+#define LCDM_MAX_DEVICES 64
+static void* g_static_ptr[LCDM_MAX_DEVICES];
+static std::mutex g_static_mu;
+
+// Device address of g_static_ws on the current device (set up on first use).
+static lcdm_status static_workspace(void** ptr) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= LCDM_MAX_DEVICES) return LCDM_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_static_mu);
+    if (!g_static_ptr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_static_ws) != cudaSuccess || !p) return LCDM_ERR_CUDA;
+        g_static_ptr[dev] = p;
+    }
+    *ptr = g_static_ptr[dev];
+    return LCDM_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+lcdm_status lcdm_distances_static(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                  int64_t n, void* const out[LCDM_NOUT], int32_t* cosmo_status,
+                                  const lcdm_opts* opts, cudaStream_t stream) {
+    if (!out || B > LCDM_STATIC_MAX_COSMOLOGIES) return LCDM_ERR_INVALID;
+    lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
+    if (st != LCDM_OK) return st;
+    void* ws = nullptr;
+    st = static_workspace(&ws);
+    if (st != LCDM_OK) return st;
+    return pairs_common(params, B, offsets, z, n, out, nullptr, nullptr, nullptr, 0, 1, nullptr, nullptr,
+                        cosmo_status, opts, ws, LCDM_STATIC_WS_BYTES, stream);
+}
+
 
 lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes) {
     if (!opts_ok(opts) || B <= 0 || !bytes) return LCDM_ERR_INVALID;
