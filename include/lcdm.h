@@ -153,7 +153,7 @@ lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* o
  * allocator at hand.  (The paper has no counterpart; this is a convenience of
  * this library.)
  *   Scratch lives in a fixed device array inside the library, sized for
- *   LCDM_STATIC_MAX_COSMOLOGIES cosmologies (about 4 MB), which stays
+ *   LCDM_STATIC_MAX_COSMOLOGIES cosmologies (about 6 MB), which stays
  *   allocated on every device that loads the library until the process exits.
  *   B larger than that is rejected with LCDM_ERR_INVALID; nothing is enqueued.
  *   The function calls no cudaMalloc, cudaFree or other allocating routine.

@@ -162,7 +162,8 @@ lcdm_status launch_plan(Plan& P, int block, int bps, cudaStream_t s) {
 
 lcdm_status run_prep(const double* params, int64_t B, const lcdm_opts* opts, const Carved& cv, int32_t* status,
                      double* grad, double* loglike, cudaStream_t s) {
-    int block = 128;
+    // one warp per block: the FP64 work spreads over as many SMs as possible
+    int block = 32;
     int64_t grid = (B + block - 1) / block;
     prep_kernel<<<(unsigned)grid, block, 0, s>>>(params, B, opts->ncol, cv.recD, cv.recF, status, grad, loglike);
     g_launches++;

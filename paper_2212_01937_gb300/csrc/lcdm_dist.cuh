@@ -36,10 +36,11 @@ template <class T> LCDM_HD T rc_any(T x, T y, int* fail) {
 }
 
 // The R_J tracks are given by h_j = p_j - x1 (their distance from the single
-// argument): the callers form h_j directly, without cancellation.
-template <int NJ, class T, class PT>
-LCDM_HD void carlson_any(T x1, PT pr, const T* h, bool needRD1, T& RF, T& RD1, T* RJ, int* fail, T* DJ = 0) {
-    T tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1];
+// argument): the callers form h_j directly, without cancellation.  NEED_RD1:
+// return R_D(x2, x3, x1); WANT_DJ: return DJ = (R_J(last track) - R_D1) / h.
+template <int NJ, bool NEED_RD1, bool WANT_DJ, class T, class PT>
+LCDM_HD void carlson_any(T x1, PT pr, const T* h, T& RF, T& RD1, T* RJ, int* fail, T* DJ = 0) {
+    T tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1], hh[NJ > 0 ? NJ : 1];
     bool pv[NJ > 0 ? NJ : 1];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
@@ -50,22 +51,23 @@ LCDM_HD void carlson_any(T x1, PT pr, const T* h, bool needRD1, T& RF, T& RD1, T
             s[j] = (x1 * (psum(pr) + q[j]) - pprod(pr)) / (x1 + q[j]);
             if (!(sval(s[j]) > 0)) *fail = 2;
             tr[j] = s[j];
+            hh[j] = s[j] - x1;
         } else {
             tr[j] = p;
+            hh[j] = h[j];
         }
     }
-    if (DJ && NJ > 0 && !pv[NJ - 1]) {
-        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, true>(x1, pr, tr, fail, h[NJ > 0 ? NJ - 1 : 0]);
+    if constexpr (WANT_DJ && NJ > 0) {
+        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, true, false>(x1, pr, tr, fail, hh[NJ - 1]);
         RF = R.RF; RD1 = R.RD1;
 #pragma unroll
         for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
         *DJ = R.DJ;
-    } else if (needRD1) {
-        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true>(x1, pr, tr, fail);
+    } else if constexpr (NEED_RD1) {
+        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, false, false>(x1, pr, tr, fail);
         RF = R.RF; RD1 = R.RD1;
 #pragma unroll
         for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
-        if (DJ && NJ > 0) *DJ = (R.RJ[NJ - 1] - RD1) / h[NJ - 1];
     } else {
         DupResult<T, NJ, PT> R = carlson_dup<T, NJ, false>(x1, pr, tr, fail);
         RF = R.RF; RD1 = RF;
@@ -79,7 +81,7 @@ LCDM_HD void carlson_any(T x1, PT pr, const T* h, bool needRD1, T& RF, T& RD1, T
             T rc = rc_value(xy + sq, sq, fail);
             RJ[j] = ((s[j] - x1) * RJ[j] - cst<T>(3.0) * RF + cst<T>(3.0) * ssqrt(x1 * xy / (xy + sq)) * rc)
                     / (q[j] + x1);
-            if (DJ && j == NJ - 1) *DJ = (RJ[j] - RD1) / h[j];
+            if (WANT_DJ && j == NJ - 1) *DJ = (RJ[j] - RD1) / h[j];
         }
     }
 }
@@ -105,14 +107,27 @@ template <class T, int K> LCDM_HD Dual<T, K> rc_any(const Dual<T, K>& x, const D
 
 // Relative spread of the arguments below which the derivative formulas lose
 // too many digits (they divide by differences of the arguments): there the
-// tangents are carried through the duplication sequence itself.
+// tangents are carried through the duplication sequence itself.  In FP32 the
+// tangents always go through the duplication sequence: measured against the
+// oracle it is the more accurate of the two at every spread (the formulas'
+// divisions by argument differences cost 2-4 more digits in FP32), and a
+// warp then runs a single code path.
 template <class T> struct Spread;
-template <> struct Spread<float> { static LCDM_HD float s0() { return 0.5f; } };
-template <> struct Spread<double> { static LCDM_HD double s0() { return 0.05; } };
-template <> struct Spread<df64> { static LCDM_HD df64 s0() { return mkdf(0.1f); } };
+template <> struct Spread<float> {
+    static LCDM_HD float s0() { return 0.5f; }
+    enum { always_dup = 1 };
+};
+template <> struct Spread<double> {
+    static LCDM_HD double s0() { return 0.05; }
+    enum { always_dup = 0 };
+};
+template <> struct Spread<df64> {
+    static LCDM_HD df64 s0() { return mkdf(0.1f); }
+    enum { always_dup = 0 };
+};
 
-template <int NJ, class T, int K, class PD>
-LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h, bool needRD1, Dual<T, K>& RF,
+template <int NJ, bool NEED_RD1, bool WANT_DJ, class T, int K, class PD>
+LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h, Dual<T, K>& RF,
                          Dual<T, K>& RD1, Dual<T, K>* RJ, int* fail, Dual<T, K>* DJ = 0) {
     typedef Dual<T, K> D;
     typedef typename PairVal<PD>::type PT;
@@ -137,7 +152,6 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h
         }
         trv[j] = tr[j].v;
     }
-    const bool ddl = DJ && NJ > 0 && !pv[NJ > 0 ? NJ - 1 : 0];
     // spread of the arguments around their mean
     T mu = xv + psum(prv);
 #pragma unroll
@@ -151,26 +165,27 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h
         if (sval(dj) > sval(dev2)) dev2 = dj;
     }
     T lim = Spread<T>::s0() * mu;
-    const bool close = sval(dev2) < sval(lim * lim);
+    // The choice is made for all lanes that run together (either result is
+    // valid for every lane): a warp then runs one of the two paths, not both.
+    const bool close = Spread<T>::always_dup || group_any(sval(dev2) < sval(lim * lim));
     D Jd[NJ > 0 ? NJ : 1];
     if (close) {
         // tangents through the duplication sequence (arguments nearly equal)
-        DupResult<D, NJ, PD> R = ddl ? carlson_dup<D, NJ, true, PD, true>(x1, pr, tr, fail, hh[NJ > 0 ? NJ - 1 : 0])
-                                     : carlson_dup<D, NJ, true, PD>(x1, pr, tr, fail);
+        DupResult<D, NJ, PD> R = carlson_dup<D, NJ, NEED_RD1 || WANT_DJ, PD, WANT_DJ, false>(
+            x1, pr, tr, fail, hh[NJ > 0 ? NJ - 1 : 0]);
         RF = R.RF;
         RD1 = R.RD1;
 #pragma unroll
         for (int j = 0; j < NJ; j++) Jd[j] = R.RJ[j];
-        if (ddl) *DJ = R.DJ;
+        if constexpr (WANT_DJ) *DJ = R.DJ;
     } else {
-        DupResult<T, NJ, PT> R = ddl ? carlson_dup<T, NJ, true, PT, true>(xv, prv, trv, fail, hh[NJ > 0 ? NJ - 1 : 0].v)
-                                     : carlson_dup<T, NJ, true, PT>(xv, prv, trv, fail);
+        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, WANT_DJ, true>(xv, prv, trv, fail, hh[NJ > 0 ? NJ - 1 : 0].v);
         // R_F, eq. (2.10)
         RF.v = R.RF;
 #pragma unroll
         for (int k = 0; k < K; k++) RF.d[k] = (R.RD1 * x1.d[k] + pdot_k(R.RDp, pr, k)) * cst<T>(-1.0 / 6.0);
         // R_D(x2, x3, x1): dR_D(x,y,z)/dx = (R_D(x,y,z) - R_D(y,z,x)) / (2 (z - x)); x1 by homogeneity
-        if (needRD1) {
+        if (NEED_RD1 || WANT_DJ) {
             PT dpair = pscale(prsub(R.RD1, R.RDp) / prsub(xv, prv), cst<T>(0.5));
             T d1 = (cst<T>(-1.5) * R.RD1 - pdot(prv, dpair)) / xv;
             RD1.v = R.RD1;
@@ -197,7 +212,7 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h
                 Jd[j].v = J;
 #pragma unroll
                 for (int k = 0; k < K; k++) Jd[j].d[k] = diag * x1.d[k] + pdot_k(dpair, pr, k) + dph * hh[j].d[k];
-                if (ddl && j == NJ - 1) {
+                if (WANT_DJ && j == NJ - 1 && !pv[j]) {
                     // Delta = (R_J(x1 + h) - R_D(x2,x3,x1)) / h and its tangent from the
                     // divided differences of eqs. (2.11)-(2.12):
                     //  dDelta/dx_m = [Delta (x1 - x_m) - (R_D1 - R_Dm)] / (2 (p - x_m)(x1 - x_m))
@@ -236,7 +251,7 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h
                     / (q[j] + x1);
         }
     }
-    if (DJ && NJ > 0 && !ddl) *DJ = (RJ[NJ - 1] - RD1) / h[NJ - 1];
+    if (WANT_DJ && NJ > 0 && pv[NJ > 0 ? NJ - 1 : 0]) *DJ = (RJ[NJ - 1] - RD1) / h[NJ - 1];
 }
 
 // Phi(w) = [R_C(1, 1-w) - (1-w)^-1/2] / w: the part of R_C(y + d, y) - y^-1/2
@@ -274,8 +289,8 @@ template <class S> LCDM_HD S phi_rc(const S& w, int* fail) {
 // with u~ = sqrt(lam) u and the terms defined in the code.
 template <class S, class PS, bool WT, bool WX>
 LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
-                               const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, S& Ichi, S& It,
-                               S& IX, int* fail) {
+                               const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, const S& qA,
+                               const S& qB, const PS& qP, const S& nrm, S& Ichi, S& It, S& IX, int* fail) {
     typedef typename Base<S>::type T;
     const T one = cst<T>(1.0), third = cst<T>(1.0 / 3.0);
     const T z2 = z * z;
@@ -283,10 +298,15 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     S XB = ssqrt(z - B);
     PS XP = psqrt(prsub(z, P));
     S ppYP = pprod(YP), ppXP = pprod(XP);
-    // u_ij of Sec. 3.1 with z1 = 0, times sqrt(lam): u_AB (real), pair (u_AP, u_AP*)
-    S uAB = XtA * XB * ppYP + YtA * YB * ppXP;
-    PS W = XP * pswap(YP);
-    PS uAP = pscale(W, XtA * YB) + pscale(pswap(W), YtA * XB);
+    // u_ij of Sec. 3.1 with z1 = 0, times sqrt(lam): u_AB (real), pair (u_AP, u_AP*),
+    // written with the ratios n_j = X_j / Y_j = sqrt(1 + z q_j), q_j = -1/r_j:
+    //   u_AB = N (n_A n_B + n_P n_P*),  u_AP = N (n_P n_A + n_P* n_B),
+    // N = Y~_A Y_B |Y_P|^2 = sqrt(E^2(0)).  The tangents of n_j are z dq_j / (2 n_j),
+    // so the arguments' tangents vanish with z without cancellation.
+    S nA = ssqrt(one + qA * z), nB = ssqrt(one + qB * z);
+    PS nP = psqrt(padd(pscale(qP, z), one));
+    S uAB = nrm * (nA * nB + pprod(nP));
+    PS uAP = pscale(pscale(nP, nA) + pscale(pswap(nP), nB), nrm);
     S x1 = uAB * uAB;
     PS pr = uAP * uAP;
     S rhoB = B + one;
@@ -299,7 +319,7 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     if (WT) p[jt] = -(mA * ppPA * rhoB * z2);          // lam u_A5^2 - x1
     if (WX) p[jx] = -(lam * ppPB * z2);                // lam u_B0^2 - x1
     S RF, RD1, RJ[NJ > 0 ? NJ : 1], DJ;
-    carlson_any<NJ>(x1, pr, p, WX, RF, RD1, RJ, fail, WX ? &DJ : (S*)0);
+    carlson_any<NJ, WX, WX>(x1, pr, p, RF, RD1, RJ, fail, &DJ);
     Ichi = RF * (z + z);                               // eq. (3.7)
     if (WT) {                                          // eq. (3.8), i = A
         S kq5 = (x1 + p[jt]) * (one + z) / ((one + epsA) * (one + epsA * (one + z)));
@@ -341,17 +361,21 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
 
 template <class S, class PS, bool WT, bool WX>
 LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, const S& YA, const PS& YP,
-                             const S& amh, S& Ichi, S& It, S& IX, int* fail) {
+                             const S& amh, const S& qA, const PS& qP, const S& nrm, S& Ichi, S& It, S& IX,
+                             int* fail) {
     typedef typename Base<S>::type T;
     const T one = cst<T>(1.0);
     const T z2 = z * z;
     S XA = ssqrt(z - A);
     PS XP = psqrt(prsub(z, P));
     S ppYP = pprod(YP), ppXP = pprod(XP);
-    // u_i of App. B.1 with z1 = 0: u_A (real) and the pair (u_P, u_P*)
-    S uA = XA * ppYP + YA * ppXP;
-    PS W = XP * pswap(YP);
-    PS uP = pscale(W, YA) + pscale(pswap(W), XA);
+    // u_i of App. B.1 with z1 = 0: u_A (real) and the pair (u_P, u_P*), from the
+    // ratios n_j = X_j / Y_j = sqrt(1 + z q_j) as in the quartic:
+    //   u_A = N (n_A + n_P n_P*),  u_P = N (n_P + n_P* n_A),  N = Y_A |Y_P|^2
+    S nA = ssqrt(one + qA * z);
+    PS nP = psqrt(padd(pscale(qP, z), one));
+    S uA = nrm * (nA + pprod(nP));
+    PS uP = pscale(nP + pscale(pswap(nP), nA), nrm);
     S x1 = uA * uA;
     PS pr = uP * uP;
     enum { NJ = WT ? 1 : 0 };
@@ -359,7 +383,7 @@ LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, 
     S rhoA = A + one;
     if (WT) p[0] = rhoA * z2;                          // u_A5^2 - x1
     S RF, RD1, RJ[1];
-    carlson_any<NJ>(x1, pr, p, WX, RF, RD1, RJ, fail);
+    carlson_any<NJ, WX, false>(x1, pr, p, RF, RD1, RJ, fail);
     Ichi = amh * RF * (z + z);                         // eq. (B.1)
     if (WT) {                                          // eq. (B.2)
         S s5 = YA * ppYP * (one + z) + XA * ppXP;

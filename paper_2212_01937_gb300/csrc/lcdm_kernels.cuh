@@ -34,7 +34,11 @@ enum RecField {
     // tangents (4 slots each: Om, OL, Or, Ok)
     RF_DA = 19, RF_DB = 23, RF_DPRE = 27, RF_DPIM = 31, RF_DAMH = 35, RF_DOK = 39,
     RF_DLAM = 43, RF_DAA = 47, RF_DMA = 51, RF_DEPSA = 55, RF_DRHOA = 59,
-    NREC = 63
+    // q_j = -1/r_j for A, B and the pair (the two real members for kinds 1/3),
+    // and the scale N = sqrt(E^2(0) / alpha_n) of the Carlson arguments
+    RF_QA = 63, RF_QB, RF_QPRE, RF_QPIM, RF_NRM,
+    RF_DQA = 68, RF_DQB = 72, RF_DQPRE = 76, RF_DQPIM = 80, RF_DNRM = 84,
+    NREC = 88
 };
 
 enum CosmoStatus {
@@ -145,8 +149,10 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
         S amh = val(rd, rf, RF_AMH, RF_DAMH);
         S YA = yval(rd, rf, RF_YA, A);
         S Pre = val(rd, rf, RF_PRE, RF_DPRE), Pim = val(rd, rf, RF_PIM, RF_DPIM);
+        S qA = val(rd, rf, RF_QA, RF_DQA), nrm = val(rd, rf, RF_NRM, RF_DNRM);
+        S qPre = val(rd, rf, RF_QPRE, RF_DQPRE), qPim = val(rd, rf, RF_QPIM, RF_DQPIM);
         if (kind == 0 || kind == 2) {
-            CPair<S> P = mkcp(mkcx<S>(Pre, Pim));
+            CPair<S> P = mkcp(mkcx<S>(Pre, Pim)), qP = mkcp(mkcx<S>(qPre, qPim));
             Cx<S> yv;
             yv.re = val(rd, rf, RF_YPRE, RF_YPRE);
             yv.im = val(rd, rf, RF_YPIM, RF_YPIM);
@@ -168,23 +174,23 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
                 S YB = yval(rd, rf, RF_YB, B);
                 quartic_integrals<S, CPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
                                                        val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
-                                                       val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, Ichi, It, IX,
-                                                       fail);
+                                                       val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, qA,
+                                                       val(rd, rf, RF_QB, RF_DQB), qP, nrm, Ichi, It, IX, fail);
             } else {
-                cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, Ichi, It, IX, fail);
+                cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, qP, nrm, Ichi, It, IX, fail);
             }
         } else {
-            RPair<S> P = mkrp<S>(Pre, Pim);
+            RPair<S> P = mkrp<S>(Pre, Pim), qP = mkrp<S>(qPre, qPim);
             RPair<S> YP = mkrp<S>(yval(rd, rf, RF_YPRE, Pre), yval(rd, rf, RF_YPIM, Pim));
             if (kind == 1) {
                 S B = val(rd, rf, RF_B, RF_DB);
                 S YB = yval(rd, rf, RF_YB, B);
                 quartic_integrals<S, RPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
                                                        val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
-                                                       val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, Ichi, It, IX,
-                                                       fail);
+                                                       val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, qA,
+                                                       val(rd, rf, RF_QB, RF_DQB), qP, nrm, Ichi, It, IX, fail);
             } else {
-                cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, Ichi, It, IX, fail);
+                cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, qP, nrm, Ichi, It, IX, fail);
             }
         }
     }

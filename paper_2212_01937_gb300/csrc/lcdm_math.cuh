@@ -379,10 +379,11 @@ template <class T, int K> struct Prec<Dual<T, K> > {
 };
 
 // R_C(x, y) = R_F(x, y, y) (eq. 2.8) by duplication; value only.
-template <class T> LCDM_HD T rc_value(T x, T y, int* fail) {
+template <class T> LCDM_NI T rc_value(T x, T y, int* fail) {
     const T tol = Prec<T>::tol();
     int m = 0;
     T A = (x + y + y) * cst<T>(1.0 / 3.0);
+#pragma unroll 1
     for (; m < Prec<T>::maxit; m++) {
         T dv = sabs(y - A);
         if (sval(dv) <= sval(tol * sabs(A))) break;
@@ -499,18 +500,29 @@ template <class T> LCDM_HD RPair<T> rd_pair_series(T x1, const RPair<T>& pr, T f
 template <class T> LCDM_HD CPair<T> pzero(const CPair<T>&) { return mkcp(mkcx<T>(cst<T>(0.0), cst<T>(0.0))); }
 template <class T> LCDM_HD RPair<T> pzero(const RPair<T>&) { return mkrp<T>(cst<T>(0.0), cst<T>(0.0)); }
 
+// Whether the predicate holds on any lane that runs this call together with
+// the calling lane (on the host: the caller's own predicate).
+LCDM_HD bool group_any(bool p) {
+#ifdef __CUDA_ARCH__
+    return __any_sync(__activemask(), p);
+#else
+    return p;
+#endif
+}
+
 LCDM_HD int even_exponent(float mag) {
     int e = (mag > 0.f && mag < 3.0e38f) ? ilogbf(mag) : 0;
     return e & ~1;
 }
 
-// One duplication sequence for R_F, R_D (all three specials when WANT_D) and
-// NJ R_J tracks with p_j > 0.  The triple is (x1, pair).  Arguments are first
-// scaled by an even power of two (exact; R_F ~ s^-1/2, R_D and R_J ~ s^-3/2).
+// One duplication sequence for R_F, R_D (x1 special when WANT_D; the pair
+// members special as well when WANT_DP) and NJ R_J tracks with p_j > 0.  The
+// triple is (x1, pair).  Arguments are first scaled by an even power of two
+// (exact; R_F ~ s^-1/2, R_D and R_J ~ s^-3/2).
 // With DDL, the last track is p = x1 + hl (hl given separately, exactly) and
 // DJ = (R_J(p) - R_D(x2, x3, x1)) / hl is evaluated term by term (sum terms
 // and the final series) so that close p and x1 cause no cancellation.
-template <class T, int NJ, bool WANT_D, class PT, bool DDL = false>
+template <class T, int NJ, bool WANT_D, class PT, bool DDL = false, bool WANT_DP = WANT_D>
 LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T hl = T()) {
     DupResult<T, NJ, PT> R;
     float mag = fabsf((float)sval(x1));
@@ -544,6 +556,7 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
     }
     const T tol = Prec<T>::tol();
     int m = 0;
+#pragma unroll 1
     for (; m < Prec<T>::maxit; m++) {
         T mu = x1 + psum(pr);
 #pragma unroll
@@ -562,10 +575,8 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         T s1 = ssqrt(x1);
         PT sp = psqrt(pr);
         T lam = s1 * psum(sp) + pprod(sp);
-        if (WANT_D) {
-            sD1 = sD1 + f / (s1 * (x1 + lam));
-            sDp = sDp + pscale(prcp(sp * padd(pr, lam)), f);
-        }
+        if (WANT_D) sD1 = sD1 + f / (s1 * (x1 + lam));
+        if (WANT_DP) sDp = sDp + pscale(prcp(sp * padd(pr, lam)), f);
 #pragma unroll
         for (int j = 0; j < NJ; j++) {
             T sq = ssqrt(p[j]);
@@ -607,8 +618,9 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         PT Y = pscale(prsub(A, pr), iA);
         T ser = rj_series<T, T>(X, psum(Y), pprod(Y), X);
         R.RD1 = sldexp(f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1, -3 * e / 2);
-        R.RDp = pldexp(rd_pair_series(x1, pr, f, sDp), -3 * e / 2);
     }
+    if (WANT_DP) R.RDp = pldexp(rd_pair_series(x1, pr, f, sDp), -3 * e / 2);
+    else R.RDp = pzero(pr);
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
         T A = (x1 + psum(pr) + cst<T>(2.0) * p[j]) * cst<T>(0.2), iA = cst<T>(1.0) / A;

@@ -25,6 +25,14 @@ LCDM_HD cd csqrt_(cd a) {
     return cmk(fabs(a.im) / (2 * t), a.im < 0 ? -t : t);
 }
 
+LCDM_HD double cnorm(cd a) { return a.re * a.re + a.im * a.im; }
+// 1/b with one real division (the polynomial's values stay far inside the
+// double range for the normalised coefficients used here)
+LCDM_HD cd crcp(cd b) {
+    double s = 1.0 / cnorm(b);
+    return cmk(b.re * s, -b.im * s);
+}
+
 // p(x) = sum_k c[k] x^k (degree n, c[n] = 1) and p'(x) by Horner's rule
 LCDM_HD void horner(const double* c, int n, cd x, cd& p, cd& dp) {
     p = cmk(c[n], 0); dp = cmk(0, 0);
@@ -35,10 +43,10 @@ LCDM_HD void horner(const double* c, int n, cd x, cd& p, cd& dp) {
 // iteration started on circles whose radii come from the Newton polygon of
 // log|c_k| (so a root near -Om/Or and the O(1) roots both start close).
 LCDM_HD int poly_roots(const double* c, int n, cd* z) {
-    // upper convex hull of (k, log|c_k|)
-    double lg[5];
+    // upper convex hull of (k, log|c_k|); single precision is enough for the start
+    float lg[5];
     int idx[5], m = 0;
-    for (int k = 0; k <= n; k++) lg[k] = c[k] != 0 ? log(fabs(c[k])) : -1e300;
+    for (int k = 0; k <= n; k++) lg[k] = c[k] != 0 ? logf((float)fabs(c[k])) : -1e30f;
     for (int k = 0; k <= n; k++) {
         if (c[k] == 0) continue;
         while (m >= 2) {
@@ -51,30 +59,31 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
     int r = 0;
     for (int e = 0; e + 1 < m; e++) {
         int a = idx[e], b = idx[e + 1], w = b - a;
-        double rad = exp((lg[a] - lg[b]) / w);
+        float rad = expf((lg[a] - lg[b]) / w);
         for (int j = 0; j < w; j++) {
-            double ang = 2.0 * CUDART_PI * j / w + 2.0 * CUDART_PI * a / n + 0.4;
-            z[r++] = cmk(rad * cos(ang), rad * sin(ang));
+            float ang = 6.2831853f * j / w + 6.2831853f * a / n + 0.4f;
+            z[r++] = cmk(rad * cosf(ang), rad * sinf(ang));
         }
     }
     for (; r < n; r++) z[r] = cmk(0.5 * r + 0.1, 0.3);  // (zero constant term etc.)
     int it = 0, settled = 0;
+#pragma unroll 1
     for (; it < 200; it++) {
         double maxrel = 0;
         for (int i = 0; i < n; i++) {
             cd p, dp;
             horner(c, n, z[i], p, dp);
             if (p.re == 0 && p.im == 0) continue;
-            cd ratio = cdiv(p, dp);
+            cd ratio = cmul(p, crcp(dp));
             cd s = cmk(0, 0);
             for (int j = 0; j < n; j++)
-                if (j != i) s = cadd(s, cdiv(cmk(1, 0), csub(z[i], z[j])));
-            cd w = cdiv(ratio, csub(cmk(1, 0), cmul(ratio, s)));
+                if (j != i) s = cadd(s, crcp(csub(z[i], z[j])));
+            cd w = cmul(ratio, crcp(csub(cmk(1, 0), cmul(ratio, s))));
             z[i] = csub(z[i], w);
-            double rel = cabs_(w) / (cabs_(z[i]) + 1e-300);
+            double rel = cnorm(w) / (cnorm(z[i]) + 1e-300);
             if (rel > maxrel) maxrel = rel;
         }
-        if (maxrel < 1e-15) { if (++settled >= 2) break; }
+        if (maxrel < 1e-30) { if (++settled >= 2) break; }
     }
     // Newton polishing
     for (int i = 0; i < n; i++) {
@@ -82,9 +91,9 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
             cd p, dp;
             horner(c, n, z[i], p, dp);
             if (dp.re == 0 && dp.im == 0) break;
-            cd zn = csub(z[i], cdiv(p, dp)), pn, dpn;
+            cd zn = csub(z[i], cmul(p, crcp(dp))), pn, dpn;
             horner(c, n, zn, pn, dpn);
-            if (cabs_(pn) <= cabs_(p)) z[i] = zn; else break;
+            if (cnorm(pn) <= cnorm(p)) z[i] = zn; else break;
         }
     }
     return it;
@@ -211,6 +220,37 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
                     rec[RF_DRHOA + k] = dA;
                 }
             }
+            // q_j = -1/r_j (dq_j = dr_j / r_j^2) for the normalised Carlson arguments
+            {
+                double rA = A.re - 1.0;
+                rec[RF_QA] = rA != 0.0 ? -1.0 / rA : 0.0;
+                for (int k = 0; k < K; k++) rec[RF_DQA + k] = rA != 0.0 ? dr[0][k].re / (rA * rA) : 0.0;
+                if (n == 4) {
+                    double rB = Bv.re - 1.0;
+                    rec[RF_QB] = rB != 0.0 ? -1.0 / rB : 0.0;
+                    for (int k = 0; k < K; k++) rec[RF_DQB + k] = rB != 0.0 ? dr[1][k].re / (rB * rB) : 0.0;
+                }
+                const int jq = n == 4 ? 2 : 1;
+                if (cpair) {
+                    cd r = cmk(P1.re - 1.0, P1.im), r2 = cmul(r, r);
+                    cd q = cdiv(cmk(-1.0, 0.0), r);
+                    rec[RF_QPRE] = q.re;
+                    rec[RF_QPIM] = q.im;
+                    for (int k = 0; k < K; k++) {
+                        cd dq = cdiv(dr[jq][k], r2);
+                        rec[RF_DQPRE + k] = dq.re;
+                        rec[RF_DQPIM + k] = dq.im;
+                    }
+                } else {
+                    double r1 = P1.re - 1.0, r2 = P2.re - 1.0;
+                    rec[RF_QPRE] = r1 != 0.0 ? -1.0 / r1 : 0.0;
+                    rec[RF_QPIM] = r2 != 0.0 ? -1.0 / r2 : 0.0;
+                    for (int k = 0; k < K; k++) {
+                        rec[RF_DQPRE + k] = r1 != 0.0 ? dr[jq][k].re / (r1 * r1) : 0.0;
+                        rec[RF_DQPIM + k] = r2 != 0.0 ? dr[jq + 1][k].re / (r2 * r2) : 0.0;
+                    }
+                }
+            }
             for (int k = 0; k < K; k++) {
                 rec[RF_DA + k] = dr[0][k].re;
                 rec[RF_DB + k] = n == 4 ? dr[1][k].re : 0.0;
@@ -228,6 +268,15 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
     rec[RF_DH] = LCDM_C_KMS / H0;
     rec[RF_TH] = LCDM_HUBBLE_GYR / H0;
     rec[RF_KIND] = kind;
+    // N = sqrt(E^2(0) / alpha_n): E^2(0) = Om + OL + Or + Ok, exactly 1 under the closure
+    const double S0 = ncol == 4 ? 1.0 : Om + OL + Or + Ok;
+    const double nrm = n == 4 ? sqrt(S0) : sqrt(S0 / Om);
+    rec[RF_NRM] = nrm;
+    for (int k = 0; k < K; k++) {
+        const double dS = ncol == 4 ? 0.0 : 1.0, dOm = k == 0 ? 1.0 : 0.0;
+        rec[RF_DNRM + k] = n == 4 ? dS / (2.0 * nrm) : (dS * Om - S0 * dOm) / (2.0 * nrm * Om * Om);
+        if (n == 3 && k == 2) rec[RF_DNRM + k] = nan("");
+    }
     for (int k = 0; k < K; k++) {
         rec[RF_DAMH + k] = 0;
         if (n == 4 && k == 2) rec[RF_DAMH + k] = -0.5 * amh / Or;
