@@ -130,6 +130,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
+    ap.add_argument("--no-vi", action="store_true", help="skip the variational-inference step timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -161,11 +162,7 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
 
     def step():
-        return lcdm.distances_vjp(params, z, cot, offsets, outputs=OUTPUTS, precision="fp32",
-                                  workspace=call.ws)
-
-    def prep_only():
-        return lcdm.roots(params)
+        return lcdm.distances_vjp(params, z, cot, offsets, outputs=OUTPUTS, call=call)
 
     for _ in range(args.warmup):
         step()
@@ -198,17 +195,13 @@ def main():
         dist.barrier()
     value = npairs * world / (ms / 1e3)
 
-    # prep share (FP64 root solve) timed alone, for the dominant-kernel duration
-    for _ in range(3):
-        prep_only()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(5):
-        prep_only()
-    e1.record()
-    torch.cuda.synchronize()
-    prep_ms = e0.elapsed_time(e1) / 5
-    pair_ms = max(ms - prep_ms, 1e-6)
+    # device time of the pair kernel alone: CUDA-graph replays of (L2 flush + step)
+    # minus replays of (L2 flush + root preparation), so host overheads drop out
+    rcall = lcdm.Call(params, torch.zeros(B, device=dev), layout="dense", precision="fp64")
+    step_g = graph_ms(lambda: (flush.zero_(), step()), dev)
+    prep_g = graph_ms(lambda: (flush.zero_(), lcdm.roots(params, call=rcall)), dev)
+    pair_ms = max(step_g - prep_g, 1e-6)
+    prep_ms = prep_g - graph_ms(lambda: flush.zero_(), dev)
 
     # end to end through the public API with host buffers (pinned)
     z_h = z.cpu().pin_memory()
@@ -269,10 +262,61 @@ def main():
                         "ms_per_step": e2e_ms},
                 "cpu_baseline": cpu}
         line.update(extra)
+        if not args.no_vi:
+            line["vi_step"] = vi_step_rate(dev)
         print(json.dumps(line))
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def graph_ms(fn, dev, reps=10):
+    """Device milliseconds per call of fn, from replays of one CUDA graph that
+    holds `reps` calls (no host work between the kernels)."""
+    import torch
+    side = torch.cuda.Stream(device=dev)
+    side.wait_stream(torch.cuda.current_stream(dev))
+    with torch.cuda.stream(side):
+        fn()
+    torch.cuda.current_stream(dev).wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        for _ in range(reps):
+            fn()
+    g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(3):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / (3 * reps)
+
+
+def vi_step_rate(dev, steps=10):
+    """One variational-inference step of the 10^6-supernova model (256 guide
+    samples x 10^6 shared redshifts: fused log-likelihood and gradient, ELBO
+    gradient, Adam), replayed from its CUDA graph."""
+    import torch
+    from paper_2212_01937_gb300 import vi, workloads
+    d = workloads.config3()
+    centre, scale = vi.default_guide(d.extra["truth"])
+    opt = vi.GaussianVI(torch.tensor(d.z, dtype=torch.float32, device=dev), torch.tensor(d.m_obs, device=dev),
+                        centre, scale, M=d.M, sigma=d.sigma, samples=256)
+    for _ in range(3):
+        opt.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        opt.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": d.name + " x 256 guide samples (configs[2]), FP32, CUDA-graph replay",
+            "ms_per_step": ms, "pairs_per_step": opt.pairs_per_step,
+            "value": opt.pairs_per_step / (ms / 1e3), "unit": UNIT}
 
 
 def fp64_baselines(lcdm, params, offsets, b, dev):

@@ -12,31 +12,68 @@ LCDM_HD cd cmk(double r, double i) { cd c; c.re = r; c.im = i; return c; }
 LCDM_HD cd cadd(cd a, cd b) { return cmk(a.re + b.re, a.im + b.im); }
 LCDM_HD cd csub(cd a, cd b) { return cmk(a.re - b.re, a.im - b.im); }
 LCDM_HD cd cmul(cd a, cd b) { return cmk(a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re); }
+// One copy of the double-precision division for all of the preparation: each
+// '/' would otherwise carry its own copy of the division's slow path.
+LCDM_NI double ddiv(double a, double b) { return a / b; }
+
 LCDM_HD cd cdiv(cd a, cd b) {
     double s = fabs(b.re) > fabs(b.im) ? fabs(b.re) : fabs(b.im);
-    double br = b.re / s, bi = b.im / s, n = br * br + bi * bi;
-    return cmk((a.re * br + a.im * bi) / (s * n), (a.im * br - a.re * bi) / (s * n));
+    double is = ddiv(1.0, s);
+    double br = b.re * is, bi = b.im * is, inv = ddiv(is, br * br + bi * bi);
+    return cmk((a.re * br + a.im * bi) * inv, (a.im * br - a.re * bi) * inv);
 }
 LCDM_HD double cabs_(cd a) { return hypot(a.re, a.im); }
 LCDM_HD cd csqrt_(cd a) {
     double r = cabs_(a);
-    if (a.re >= 0) { double t = sqrt(0.5 * (r + a.re)); return cmk(t, t > 0 ? a.im / (2 * t) : 0.0); }
+    if (a.re >= 0) { double t = sqrt(0.5 * (r + a.re)); return cmk(t, t > 0 ? a.im * ddiv(0.5, t) : 0.0); }
     double t = sqrt(0.5 * (r - a.re));
-    return cmk(fabs(a.im) / (2 * t), a.im < 0 ? -t : t);
+    return cmk(fabs(a.im) * ddiv(0.5, t), a.im < 0 ? -t : t);
 }
 
 LCDM_HD double cnorm(cd a) { return a.re * a.re + a.im * a.im; }
 // 1/b with one real division (the polynomial's values stay far inside the
 // double range for the normalised coefficients used here)
 LCDM_HD cd crcp(cd b) {
-    double s = 1.0 / cnorm(b);
+    double s = ddiv(1.0, cnorm(b));
     return cmk(b.re * s, -b.im * s);
 }
 
 // p(x) = sum_k c[k] x^k (degree n, c[n] = 1) and p'(x) by Horner's rule
 LCDM_HD void horner(const double* c, int n, cd x, cd& p, cd& dp) {
     p = cmk(c[n], 0); dp = cmk(0, 0);
+#pragma unroll 1
     for (int k = n - 1; k >= 0; k--) { dp = cadd(cmul(dp, x), p); p = cadd(cmul(p, x), cmk(c[k], 0)); }
+}
+
+// Single-precision elementary functions for the starting circles only (no
+// accuracy needed there): the fast hardware approximations on the device.
+LCDM_HD float flog(float x) {
+#ifdef __CUDA_ARCH__
+    return __logf(x);
+#else
+    return logf(x);
+#endif
+}
+LCDM_HD float fexp(float x) {
+#ifdef __CUDA_ARCH__
+    return __expf(x);
+#else
+    return expf(x);
+#endif
+}
+LCDM_HD float fcos(float x) {
+#ifdef __CUDA_ARCH__
+    return __cosf(x);
+#else
+    return cosf(x);
+#endif
+}
+LCDM_HD float fsin(float x) {
+#ifdef __CUDA_ARCH__
+    return __sinf(x);
+#else
+    return sinf(x);
+#endif
 }
 
 // Roots of the monic polynomial c (degree n <= 4) by the Aberth-Ehrlich
@@ -46,7 +83,7 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
     // upper convex hull of (k, log|c_k|); single precision is enough for the start
     float lg[5];
     int idx[5], m = 0;
-    for (int k = 0; k <= n; k++) lg[k] = c[k] != 0 ? logf((float)fabs(c[k])) : -1e30f;
+    for (int k = 0; k <= n; k++) lg[k] = c[k] != 0 ? flog((float)fabs(c[k])) : -1e30f;
     for (int k = 0; k <= n; k++) {
         if (c[k] == 0) continue;
         while (m >= 2) {
@@ -59,34 +96,37 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
     int r = 0;
     for (int e = 0; e + 1 < m; e++) {
         int a = idx[e], b = idx[e + 1], w = b - a;
-        float rad = expf((lg[a] - lg[b]) / w);
+        float rad = fexp((lg[a] - lg[b]) / w);
         for (int j = 0; j < w; j++) {
             float ang = 6.2831853f * j / w + 6.2831853f * a / n + 0.4f;
-            z[r++] = cmk(rad * cosf(ang), rad * sinf(ang));
+            z[r++] = cmk(rad * fcos(ang), rad * fsin(ang));
         }
     }
     for (; r < n; r++) z[r] = cmk(0.5 * r + 0.1, 0.3);  // (zero constant term etc.)
     int it = 0, settled = 0;
 #pragma unroll 1
     for (; it < 200; it++) {
-        double maxrel = 0;
+        bool small = true;
+#pragma unroll 1
         for (int i = 0; i < n; i++) {
             cd p, dp;
             horner(c, n, z[i], p, dp);
             if (p.re == 0 && p.im == 0) continue;
             cd ratio = cmul(p, crcp(dp));
             cd s = cmk(0, 0);
+#pragma unroll 1
             for (int j = 0; j < n; j++)
                 if (j != i) s = cadd(s, crcp(csub(z[i], z[j])));
             cd w = cmul(ratio, crcp(csub(cmk(1, 0), cmul(ratio, s))));
             z[i] = csub(z[i], w);
-            double rel = cnorm(w) / (cnorm(z[i]) + 1e-300);
-            if (rel > maxrel) maxrel = rel;
+            if (!(cnorm(w) < 1e-30 * (cnorm(z[i]) + 1e-300))) small = false;
         }
-        if (maxrel < 1e-30) { if (++settled >= 2) break; }
+        if (small) { if (++settled >= 2) break; }
     }
     // Newton polishing
+    #pragma unroll 1
     for (int i = 0; i < n; i++) {
+        #pragma unroll 1
         for (int k = 0; k < 2; k++) {
             cd p, dp;
             horner(c, n, z[i], p, dp);
@@ -100,11 +140,12 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
 }
 
 LCDM_HD void polish_real(const double* c, int n, double& x) {
+    #pragma unroll 1
     for (int k = 0; k < 3; k++) {
         double p = c[n], dp = 0;
         for (int j = n - 1; j >= 0; j--) { dp = dp * x + p; p = p * x + c[j]; }
         if (dp == 0) return;
-        double xn = x - p / dp, pn = c[n];
+        double xn = x - ddiv(p, dp), pn = c[n];
         for (int j = n - 1; j >= 0; j--) pn = pn * xn + c[j];
         if (fabs(pn) <= fabs(p)) x = xn; else return;
     }
@@ -126,18 +167,22 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
     double an = alpha[n];
     double c[5];
     if (st == ST_OK) {
-        for (int k = 0; k <= n; k++) c[k] = alpha[k] / an;
+        const double ian = ddiv(1.0, an);
+        for (int k = 0; k <= n; k++) c[k] = alpha[k] * ian;
         c[n] = 1.0;
         poly_roots(c, n, z);
         // classification: real when the imaginary part is negligible
         int nreal = 0, ir[4], ic[4], ncx = 0;
+        #pragma unroll 1
         for (int i = 0; i < n; i++) {
             if (fabs(z[i].im) <= 1e-12 * cabs_(z[i])) { z[i].im = 0; polish_real(c, n, z[i].re); ir[nreal++] = i; }
             else ic[ncx++] = i;
         }
+        #pragma unroll 1
         for (int i = 0; i < nreal; i++)
             if (z[ir[i]].re >= 1.0) st = ST_NO_BIG_BANG;   // real root at z >= 0 (Sec. 3, Fig. 1)
         // order reals by decreasing |rho| (fn15: largest roots of E^2(z+1))
+        #pragma unroll 1
         for (int i = 0; i < nreal; i++)
             for (int j = i + 1; j < nreal; j++)
                 if (fabs(z[ir[j]].re) > fabs(z[ir[i]].re)) { int t = ir[i]; ir[i] = ir[j]; ir[j] = t; }
@@ -179,11 +224,14 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
             else { rec[RF_YPRE] = sqrt(-rec[RF_PRE]); rec[RF_YPIM] = sqrt(-rec[RF_PIM]); }
             // App. A: d rho_j / d c_i = -rho_j^i / prod_{m != j} (rho_j - rho_m)  (eqs. A.2-A.4)
             cd dr[4][4];
+            #pragma unroll 1
             for (int j = 0; j < nr; j++) {
                 cd den = cmk(1, 0);
+                #pragma unroll 1
                 for (int m2 = 0; m2 < nr; m2++)
                     if (m2 != j) den = cmul(den, csub(rho[j], rho[m2]));
                 if (den.re == 0 && den.im == 0) st = (st == ST_OK) ? ST_DEGENERATE : st;
+                #pragma unroll 1
                 for (int k = 0; k < K; k++) {
                     // d alpha / d theta_k; theta = (Om, OL, Or[, Ok]); closure couples Ok
                     double da[5] = {0, 0, 0, 0, 0};
@@ -193,8 +241,9 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
                     if (k == 3) da[2] = 1;
                     if (ncol == 4) da[2] -= 1;
                     cd s = cmk(0, 0), pw = cmk(1, 0);
+                    #pragma unroll 1
                     for (int i = 0; i < n; i++) {
-                        double dci = (da[i] * an - alpha[i] * da[n]) / (an * an);
+                        double dci = (da[i] * an - alpha[i] * da[n]) * (ian * ian);
                         s = cadd(s, cmul(pw, cmk(dci, 0)));
                         pw = cmul(pw, rho[j]);
                     }
@@ -209,26 +258,30 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
                 rec[RF_LAM] = Or;
                 rec[RF_AA] = -Or * (rA - 1.0);
                 rec[RF_MA] = Or * rA;
-                rec[RF_EPSA] = -1.0 / rA;
+                const double irA = ddiv(1.0, rA);
+                rec[RF_EPSA] = -irA;
                 rec[RF_RHOA] = rA;
+                #pragma unroll 1
                 for (int k = 0; k < K; k++) {
                     double dl = (k == 2) ? 1.0 : 0.0, dA = dr[0][k].re;
                     rec[RF_DLAM + k] = dl;
                     rec[RF_DAA + k] = -(dl * (rA - 1.0) + Or * dA);
                     rec[RF_DMA + k] = dl * rA + Or * dA;
-                    rec[RF_DEPSA + k] = dA / (rA * rA);
+                    rec[RF_DEPSA + k] = dA * (irA * irA);
                     rec[RF_DRHOA + k] = dA;
                 }
             }
             // q_j = -1/r_j (dq_j = dr_j / r_j^2) for the normalised Carlson arguments
             {
                 double rA = A.re - 1.0;
-                rec[RF_QA] = rA != 0.0 ? -1.0 / rA : 0.0;
-                for (int k = 0; k < K; k++) rec[RF_DQA + k] = rA != 0.0 ? dr[0][k].re / (rA * rA) : 0.0;
+                const double iA = rA != 0.0 ? ddiv(1.0, rA) : 0.0;
+                rec[RF_QA] = -iA;
+                for (int k = 0; k < K; k++) rec[RF_DQA + k] = dr[0][k].re * (iA * iA);
                 if (n == 4) {
                     double rB = Bv.re - 1.0;
-                    rec[RF_QB] = rB != 0.0 ? -1.0 / rB : 0.0;
-                    for (int k = 0; k < K; k++) rec[RF_DQB + k] = rB != 0.0 ? dr[1][k].re / (rB * rB) : 0.0;
+                    const double iB = rB != 0.0 ? ddiv(1.0, rB) : 0.0;
+                    rec[RF_QB] = -iB;
+                    for (int k = 0; k < K; k++) rec[RF_DQB + k] = dr[1][k].re * (iB * iB);
                 }
                 const int jq = n == 4 ? 2 : 1;
                 if (cpair) {
@@ -243,14 +296,16 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
                     }
                 } else {
                     double r1 = P1.re - 1.0, r2 = P2.re - 1.0;
-                    rec[RF_QPRE] = r1 != 0.0 ? -1.0 / r1 : 0.0;
-                    rec[RF_QPIM] = r2 != 0.0 ? -1.0 / r2 : 0.0;
+                    const double i1 = r1 != 0.0 ? ddiv(1.0, r1) : 0.0, i2 = r2 != 0.0 ? ddiv(1.0, r2) : 0.0;
+                    rec[RF_QPRE] = -i1;
+                    rec[RF_QPIM] = -i2;
                     for (int k = 0; k < K; k++) {
-                        rec[RF_DQPRE + k] = r1 != 0.0 ? dr[jq][k].re / (r1 * r1) : 0.0;
-                        rec[RF_DQPIM + k] = r2 != 0.0 ? dr[jq + 1][k].re / (r2 * r2) : 0.0;
+                        rec[RF_DQPRE + k] = dr[jq][k].re * (i1 * i1);
+                        rec[RF_DQPIM + k] = dr[jq + 1][k].re * (i2 * i2);
                     }
                 }
             }
+            #pragma unroll 1
             for (int k = 0; k < K; k++) {
                 rec[RF_DA + k] = dr[0][k].re;
                 rec[RF_DB + k] = n == 4 ? dr[1][k].re : 0.0;
@@ -261,26 +316,31 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
         }
     }
     // prefactors: alpha_m^-1/2 (Or for the quartic, Om for the cubic, eq. 3.2 / fn13)
-    double amh = 1.0 / sqrt(n == 4 ? Or : Om);
+    double amh = ddiv(1.0, sqrt(n == 4 ? Or : Om));
     rec[RF_AMH] = amh;
     rec[RF_OK] = Ok;
     rec[RF_H0] = H0;
-    rec[RF_DH] = LCDM_C_KMS / H0;
-    rec[RF_TH] = LCDM_HUBBLE_GYR / H0;
+    const double iH0 = ddiv(1.0, H0);
+    rec[RF_DH] = LCDM_C_KMS * iH0;
+    rec[RF_TH] = LCDM_HUBBLE_GYR * iH0;
     rec[RF_KIND] = kind;
     // N = sqrt(E^2(0) / alpha_n): E^2(0) = Om + OL + Or + Ok, exactly 1 under the closure
     const double S0 = ncol == 4 ? 1.0 : Om + OL + Or + Ok;
-    const double nrm = n == 4 ? sqrt(S0) : sqrt(S0 / Om);
+    const double iOm = ddiv(1.0, Om);
+    const double nrm = n == 4 ? sqrt(S0) : sqrt(S0 * iOm);
+    const double inrm = ddiv(1.0, nrm);
     rec[RF_NRM] = nrm;
+    #pragma unroll 1
     for (int k = 0; k < K; k++) {
         const double dS = ncol == 4 ? 0.0 : 1.0, dOm = k == 0 ? 1.0 : 0.0;
-        rec[RF_DNRM + k] = n == 4 ? dS / (2.0 * nrm) : (dS * Om - S0 * dOm) / (2.0 * nrm * Om * Om);
+        rec[RF_DNRM + k] = n == 4 ? 0.5 * dS * inrm : 0.5 * (dS * Om - S0 * dOm) * inrm * (iOm * iOm);
         if (n == 3 && k == 2) rec[RF_DNRM + k] = nan("");
     }
+    #pragma unroll 1
     for (int k = 0; k < K; k++) {
         rec[RF_DAMH + k] = 0;
-        if (n == 4 && k == 2) rec[RF_DAMH + k] = -0.5 * amh / Or;
-        if (n == 3 && k == 0) rec[RF_DAMH + k] = -0.5 * amh / Om;
+        if (n == 4 && k == 2) rec[RF_DAMH + k] = -0.5 * amh * amh * amh;
+        if (n == 3 && k == 0) rec[RF_DAMH + k] = -0.5 * amh * amh * amh;
         if (n == 3 && k == 2) rec[RF_DAMH + k] = nan("");
         rec[RF_DOK + k] = ncol == 4 ? -1.0 : (k == 3 ? 1.0 : 0.0);
     }
@@ -298,6 +358,7 @@ __global__ void prep_kernel(const double* __restrict__ params, int64_t B, int nc
     int st = prep_one(params + b * ncol, ncol, rec);
     double* rd = recD + b * NREC;
     float2* rf = recF + b * NREC;
+    #pragma unroll 1
     for (int i = 0; i < NREC; i++) {
         rd[i] = rec[i];
         float h = (float)rec[i];

@@ -139,9 +139,11 @@ class Call:
         return (ctypes.byref(self.opts), _ptr(self.ws), self.ws_bytes, _stream(self.device))
 
 
-def roots(params):
-    """Roots of E^2 in z with their derivatives (lcdm_roots)."""
-    c = Call(params, torch.zeros(params.shape[0], device=params.device), layout="dense", precision="fp64")
+def roots(params, call=None):
+    """Roots of E^2 in z with their derivatives (lcdm_roots).  A prepared
+    ``call`` (dense layout, FP64, same params) skips the argument set-up."""
+    c = call if call is not None else Call(params, torch.zeros(params.shape[0], device=params.device),
+                                           layout="dense", precision="fp64")
     r = torch.empty(c.B, 4, 2, dtype=torch.float64, device=c.device)
     dr = torch.empty(c.B, 4, 2, c.ncol - 1, dtype=torch.float64, device=c.device)
     kind = torch.empty(c.B, dtype=torch.int32, device=c.device)
@@ -173,10 +175,11 @@ def distances_jac(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), jac_
     return out
 
 
-def distances_vjp(params, z, cot, offsets=None, outputs=(), **kw):
+def distances_vjp(params, z, cot, offsets=None, outputs=(), call=None, **kw):
     """Fused forward + adjoint (lcdm_distances_vjp): grad [B, ncol] of
-    sum_o <cot[o], out_o>.  cot: {name: tensor [npairs]}."""
-    c = Call(params, z, offsets, **kw)
+    sum_o <cot[o], out_o>.  cot: {name: tensor [npairs]}.  A prepared
+    ``call`` (same params, z, offsets) skips the argument set-up."""
+    c = call if call is not None else Call(params, z, offsets, **kw)
     out, vp = c.out_buffers(outputs)
     cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items() if v is not None}
     cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])
