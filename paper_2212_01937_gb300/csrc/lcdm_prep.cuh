@@ -103,10 +103,57 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
         }
     }
     for (; r < n; r++) z[r] = cmk(0.5 * r + 0.1, 0.3);  // (zero constant term etc.)
+    // single-precision iterations to about 1e-6 relative (short latency chains),
+    // then double precision from there (cubic convergence: two or three steps)
+    {
+        float cf[5], zr[4], zi[4];
+        for (int k = 0; k <= n; k++) cf[k] = (float)c[k];
+        for (int i = 0; i < n; i++) { zr[i] = (float)z[i].re; zi[i] = (float)z[i].im; }
+#pragma unroll 1
+        for (int itf = 0; itf < 100; itf++) {
+            bool small = true;
+#pragma unroll 1
+            for (int i = 0; i < n; i++) {
+                float pr = cf[n], pi = 0.f, dr = 0.f, di = 0.f;
+#pragma unroll 1
+                for (int k = n - 1; k >= 0; k--) {
+                    float ndr = dr * zr[i] - di * zi[i] + pr, ndi = dr * zi[i] + di * zr[i] + pi;
+                    float npr = pr * zr[i] - pi * zi[i] + cf[k], npi = pr * zi[i] + pi * zr[i];
+                    dr = ndr; di = ndi; pr = npr; pi = npi;
+                }
+                float dn = dr * dr + di * di;
+                if ((pr == 0.f && pi == 0.f) || !(dn > 0.f)) continue;
+                float idn = 1.0f / dn;
+                float rr = (pr * dr + pi * di) * idn, ri = (pi * dr - pr * di) * idn;   // p / p'
+                float sr = 0.f, si = 0.f;
+#pragma unroll 1
+                for (int j = 0; j < n; j++) {
+                    if (j == i) continue;
+                    float ar = zr[i] - zr[j], ai = zi[i] - zi[j], an2 = ar * ar + ai * ai;
+                    if (!(an2 > 0.f)) continue;
+                    float ia = 1.0f / an2;
+                    sr += ar * ia; si -= ai * ia;
+                }
+                float qr = 1.f - (rr * sr - ri * si), qi = -(rr * si + ri * sr);
+                float qn = qr * qr + qi * qi;
+                if (!(qn > 0.f)) continue;
+                float iq = 1.0f / qn;
+                float wr = (rr * qr + ri * qi) * iq, wi = (ri * qr - rr * qi) * iq;
+                zr[i] -= wr; zi[i] -= wi;
+                if (!(wr * wr + wi * wi < 1e-12f * (zr[i] * zr[i] + zi[i] * zi[i]) + 1e-30f)) small = false;
+            }
+            if (small) break;
+        }
+        for (int i = 0; i < n; i++)
+            if (isfinite(zr[i]) && isfinite(zi[i])) z[i] = cmk(zr[i], zi[i]);
+    }
+    // stop after two sweeps with every correction below 1e-15 relative, or once
+    // the corrections stop shrinking (rounding level of a near-multiple root)
     int it = 0, settled = 0;
+    double prev = 1e300;
 #pragma unroll 1
     for (; it < 200; it++) {
-        bool small = true;
+        double worst = 0.0;
 #pragma unroll 1
         for (int i = 0; i < n; i++) {
             cd p, dp;
@@ -119,9 +166,12 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
                 if (j != i) s = cadd(s, crcp(csub(z[i], z[j])));
             cd w = cmul(ratio, crcp(csub(cmk(1, 0), cmul(ratio, s))));
             z[i] = csub(z[i], w);
-            if (!(cnorm(w) < 1e-30 * (cnorm(z[i]) + 1e-300))) small = false;
+            const double rel = cnorm(w) * ddiv(1.0, cnorm(z[i]) + 1e-300);
+            if (!(rel <= worst)) worst = rel;
         }
-        if (small) { if (++settled >= 2) break; }
+        if (worst < 1e-30) { if (++settled >= 2) break; }
+        else if (it >= 4 && worst >= 0.25 * prev) break;
+        prev = worst;
     }
     // Newton polishing
     #pragma unroll 1
@@ -222,33 +272,30 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
             rec[RF_YB] = sqrt(-rec[RF_B]);
             if (cpair) { cd y = csqrt_(cmk(-rec[RF_PRE], -rec[RF_PIM])); rec[RF_YPRE] = y.re; rec[RF_YPIM] = y.im; }
             else { rec[RF_YPRE] = sqrt(-rec[RF_PRE]); rec[RF_YPIM] = sqrt(-rec[RF_PIM]); }
-            // App. A: d rho_j / d c_i = -rho_j^i / prod_{m != j} (rho_j - rho_m)  (eqs. A.2-A.4)
+            // App. A (eqs. A.2-A.4): d rho_j / d c_i = -rho_j^i / prod_{m != j} (rho_j - rho_m).
+            // Summed over the coefficients c_i = alpha_i / alpha_n of the monic
+            // polynomial this is
+            //   d rho_j / d theta_k = -(dE^2/dtheta_k)(rho_j) / (alpha_n prod_{m != j} (rho_j - rho_m)),
+            // with dE^2/dOm = x^3, dE^2/dOL = 1, dE^2/dOr = x^4, dE^2/dOk = x^2, and
+            // -x^2 added to the first three under the closure.
             cd dr[4][4];
             #pragma unroll 1
             for (int j = 0; j < nr; j++) {
-                cd den = cmk(1, 0);
+                const cd x = rho[j], x2 = cmul(x, x), x3 = cmul(x2, x), x4 = cmul(x3, x);
+                cd e2p = cmk(an, 0);
                 #pragma unroll 1
                 for (int m2 = 0; m2 < nr; m2++)
-                    if (m2 != j) den = cmul(den, csub(rho[j], rho[m2]));
-                if (den.re == 0 && den.im == 0) st = (st == ST_OK) ? ST_DEGENERATE : st;
+                    if (m2 != j) e2p = cmul(e2p, csub(x, rho[m2]));
+                const bool degenerate = e2p.re == 0 && e2p.im == 0;
+                if (degenerate) st = (st == ST_OK) ? ST_DEGENERATE : st;
+                const cd inv = degenerate ? cmk(0, 0) : crcp(e2p);
+                const double cl = ncol == 4 ? 1.0 : 0.0;
+                const cd g[4] = {csub(x3, cmul(cmk(cl, 0), x2)), csub(cmk(1, 0), cmul(cmk(cl, 0), x2)),
+                                 csub(x4, cmul(cmk(cl, 0), x2)), x2};
                 #pragma unroll 1
                 for (int k = 0; k < K; k++) {
-                    // d alpha / d theta_k; theta = (Om, OL, Or[, Ok]); closure couples Ok
-                    double da[5] = {0, 0, 0, 0, 0};
-                    if (k == 0) da[3] = 1;
-                    if (k == 1) da[0] = 1;
-                    if (k == 2) da[4] = 1;
-                    if (k == 3) da[2] = 1;
-                    if (ncol == 4) da[2] -= 1;
-                    cd s = cmk(0, 0), pw = cmk(1, 0);
-                    #pragma unroll 1
-                    for (int i = 0; i < n; i++) {
-                        double dci = (da[i] * an - alpha[i] * da[n]) * (ian * ian);
-                        s = cadd(s, cmul(pw, cmk(dci, 0)));
-                        pw = cmul(pw, rho[j]);
-                    }
-                    dr[j][k] = cmk(0, 0);
-                    if (den.re != 0 || den.im != 0) dr[j][k] = cdiv(cmk(-s.re, -s.im), den);
+                    cd d = cmul(g[k], inv);
+                    dr[j][k] = cmk(-d.re, -d.im);
                     if (n == 3 && k == 2) dr[j][k] = cmk(nan(""), nan(""));  // no Or direction in a cubic
                 }
             }
