@@ -143,6 +143,31 @@ lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* o
                                double* grad, void* mu_out, int32_t* cosmo_status, const lcdm_opts* opts,
                                void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* Device workspace, in bytes, of lcdm_distances_vjp_host for B cosmologies
+ * and n pairs (records, parameters, offsets, status, gradient, and the z,
+ * cotangent and output arrays of all six outputs). */
+lcdm_status lcdm_host_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts, size_t* bytes);
+
+/* lcdm_distances_vjp for data held in HOST memory: params [B][ncol],
+ * offsets [B+1], z [n], cot[o] [n], out[o] [n] (out and each entry may be
+ * NULL), grad [B][ncol] and cosmo_status [B] are all host arrays; CSR layout
+ * only.  The paper's method is unchanged (Sec. 3); this entry point only moves
+ * the data.  The batch is cut into nchunks (1..64) runs of whole rows with
+ * about n / nchunks pairs each; the host-to-device copies of the next run and
+ * the device-to-host copies of the previous one overlap the pair kernel of the
+ * current run.  The copies run on two streams that the library creates once
+ * per device (first call); the kernels run on `stream`, after the work already
+ * queued there.  Page-locked host arrays are needed for the copies to overlap.
+ *   dws: device workspace of lcdm_host_workspace_size(B, n, opts) bytes,
+ *        256-byte aligned.
+ * The call returns when every result is in the host arrays.  Calls on one
+ * device share the internal streams: they must not run concurrently from
+ * several host threads.                                                     */
+lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                    int64_t n, const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT],
+                                    double* grad, int32_t* cosmo_status, const lcdm_opts* opts, void* dws,
+                                    size_t dws_bytes, int32_t nchunks, cudaStream_t stream);
+
 /* Largest B accepted by lcdm_distances_static. */
 #define LCDM_STATIC_MAX_COSMOLOGIES 4096
 

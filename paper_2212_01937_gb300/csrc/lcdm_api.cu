@@ -241,6 +241,68 @@ static lcdm_status static_workspace(void** ptr) {
     return LCDM_OK;
 }
 
+// ----------------------------------------------------------------------------
+// Host-buffer entry point: chunked copies on two internal streams per device
+// (host-to-device and device-to-host) overlapping the pair kernel of the
+// neighbouring chunks on the caller's stream.
+// ----------------------------------------------------------------------------
+#define LCDM_HOST_MAX_CHUNKS 64
+struct HostStreams {
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev[2 * LCDM_HOST_MAX_CHUNKS + 3];
+    bool ready = false;
+};
+static HostStreams g_host_streams[LCDM_MAX_DEVICES];
+static std::mutex g_host_mu;
+
+lcdm_status host_streams(HostStreams** out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= LCDM_MAX_DEVICES) return LCDM_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    HostStreams& h = g_host_streams[dev];
+    if (!h.ready) {
+        if (cudaStreamCreateWithFlags(&h.up, cudaStreamNonBlocking) != cudaSuccess) return LCDM_ERR_CUDA;
+        if (cudaStreamCreateWithFlags(&h.down, cudaStreamNonBlocking) != cudaSuccess) return LCDM_ERR_CUDA;
+        for (int i = 0; i < 2 * LCDM_HOST_MAX_CHUNKS + 3; i++)
+            if (cudaEventCreateWithFlags(&h.ev[i], cudaEventDisableTiming) != cudaSuccess) return LCDM_ERR_CUDA;
+        h.ready = true;
+    }
+    *out = &h;
+    return LCDM_OK;
+}
+
+// Device workspace of the host entry point: records, then params, offsets,
+// status, grad, z, six cotangent and six output arrays.
+struct HostCarve {
+    Carved rec;
+    double* params;
+    int64_t* offsets;
+    int32_t* status;
+    double* grad;
+    char* z;
+    char* cot[LCDM_NOUT];
+    char* out[LCDM_NOUT];
+    size_t bytes;
+};
+
+HostCarve host_carve(char* base, int64_t B, int64_t n, int ncol, size_t es) {
+    HostCarve c;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+    char* rec = take(ws_bytes_for(B));
+    c.rec.recD = (double*)rec;
+    c.rec.recF = rec ? (float2*)(rec + align256((size_t)B * NREC * sizeof(double))) : nullptr;
+    c.params = (double*)take((size_t)B * ncol * sizeof(double));
+    c.offsets = (int64_t*)take((size_t)(B + 1) * sizeof(int64_t));
+    c.status = (int32_t*)take((size_t)B * sizeof(int32_t));
+    c.grad = (double*)take((size_t)B * ncol * sizeof(double));
+    c.z = take((size_t)n * es);
+    for (int i = 0; i < LCDM_NOUT; i++) c.cot[i] = take((size_t)n * es);
+    for (int i = 0; i < LCDM_NOUT; i++) c.out[i] = take((size_t)n * es);
+    c.bytes = off;
+    return c;
+}
+
 }  // namespace
 
 extern "C" {
@@ -258,6 +320,98 @@ lcdm_status lcdm_distances_static(const double* params, int64_t B, const int64_t
                         cosmo_status, opts, ws, LCDM_STATIC_WS_BYTES, stream);
 }
 
+
+lcdm_status lcdm_host_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts, size_t* bytes) {
+    if (!opts_ok(opts) || B <= 0 || n < 0 || !bytes) return LCDM_ERR_INVALID;
+    const size_t es = opts->precision == LCDM_FP64 ? 8 : 4;
+    *bytes = host_carve(nullptr, B, n, opts->ncol, es).bytes;
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                    int64_t n, const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT],
+                                    double* grad, int32_t* cosmo_status, const lcdm_opts* opts, void* dws,
+                                    size_t dws_bytes, int32_t nchunks, cudaStream_t stream) {
+    if (!opts_ok(opts) || opts->layout != LCDM_LAYOUT_CSR || !params || !offsets || B <= 0 || n < 0 ||
+        (n > 0 && !z) || !cot || !grad || !cosmo_status || nchunks < 1 || nchunks > LCDM_HOST_MAX_CHUNKS)
+        return LCDM_ERR_INVALID;
+    if (offsets[0] != 0 || offsets[B] != n) return LCDM_ERR_INVALID;
+    for (int64_t r = 0; r < B; r++)
+        if (offsets[r + 1] < offsets[r]) return LCDM_ERR_INVALID;
+    const int ncol = opts->ncol;
+    const size_t es = opts->precision == LCDM_FP64 ? 8 : 4;
+    if (!dws || ((uintptr_t)dws & 255) != 0) return LCDM_ERR_WORKSPACE;
+    HostCarve d = host_carve((char*)dws, B, n, ncol, es);
+    if (dws_bytes < d.bytes) return LCDM_ERR_WORKSPACE;
+    HostStreams* hs = nullptr;
+    lcdm_status st = host_streams(&hs);
+    if (st != LCDM_OK) return st;
+    cudaEvent_t* ev = hs->ev;
+    bool ok = true;
+    auto chk = [&](cudaError_t e) { ok = ok && e == cudaSuccess; };
+    // the copies wait for earlier work on the caller's stream (workspace reuse)
+    chk(cudaEventRecord(ev[0], stream));
+    chk(cudaStreamWaitEvent(hs->up, ev[0], 0));
+    chk(cudaMemcpyAsync(d.params, params, (size_t)B * ncol * sizeof(double), cudaMemcpyHostToDevice, hs->up));
+    chk(cudaMemcpyAsync(d.offsets, offsets, (size_t)(B + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, hs->up));
+    chk(cudaEventRecord(ev[1], hs->up));
+    chk(cudaStreamWaitEvent(stream, ev[1], 0));
+    if (!ok) return LCDM_ERR_CUDA;
+    st = run_prep(d.params, B, opts, d.rec, d.status, d.grad, nullptr, stream);
+    if (st != LCDM_OK) return st;
+    // chunk c covers rows [rb[c], rb[c+1]) with about n / nchunks pairs each
+    int64_t rb[LCDM_HOST_MAX_CHUNKS + 1];
+    rb[0] = 0;
+    for (int c = 1; c < nchunks; c++) {
+        const int64_t target = n * c / nchunks;
+        int64_t lo = rb[c - 1], hi = B;   // first row whose start offset is >= target
+        while (lo < hi) {
+            int64_t mid = (lo + hi) / 2;
+            if (offsets[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        rb[c] = lo;
+    }
+    rb[nchunks] = B;
+    for (int c = 0; c < nchunks; c++) {
+        const int64_t r0 = rb[c], r1 = rb[c + 1];
+        const int64_t o0 = offsets[r0], o1 = offsets[r1];
+        if (r1 <= r0 || o1 <= o0) continue;
+        const size_t nb = (size_t)(o1 - o0) * es, ob = (size_t)o0 * es;
+        chk(cudaMemcpyAsync(d.z + ob, (const char*)z + ob, nb, cudaMemcpyHostToDevice, hs->up));
+        const void* cotd[LCDM_NOUT] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        void* outd[LCDM_NOUT] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+        for (int i = 0; i < LCDM_NOUT; i++) {
+            if (cot[i]) {
+                chk(cudaMemcpyAsync(d.cot[i] + ob, (const char*)cot[i] + ob, nb, cudaMemcpyHostToDevice, hs->up));
+                cotd[i] = d.cot[i];
+            }
+            if (out && out[i]) outd[i] = d.out[i];
+        }
+        chk(cudaEventRecord(ev[2 + 2 * c], hs->up));
+        chk(cudaStreamWaitEvent(stream, ev[2 + 2 * c], 0));
+        if (!ok) return LCDM_ERR_CUDA;
+        Carved rc;
+        rc.recD = d.rec.recD + r0 * NREC;
+        rc.recF = d.rec.recF + r0 * NREC;
+        Plan P;
+        make_plan(d.params + r0 * ncol, r1 - r0, d.offsets + r0, d.z, o1 - o0, outd, nullptr, cotd, nullptr, 0, 1,
+                  d.grad + r0 * ncol, nullptr, d.status + r0, opts, rc, P);
+        P.args.base = o0;
+        st = launch_plan(P, opts->block, opts->blocks_per_sm, stream);
+        if (st != LCDM_OK) return st;
+        chk(cudaEventRecord(ev[3 + 2 * c], stream));
+        chk(cudaStreamWaitEvent(hs->down, ev[3 + 2 * c], 0));
+        for (int i = 0; i < LCDM_NOUT; i++)
+            if (outd[i]) chk(cudaMemcpyAsync((char*)out[i] + ob, d.out[i] + ob, nb, cudaMemcpyDeviceToHost, hs->down));
+        if (!ok) return LCDM_ERR_CUDA;
+    }
+    chk(cudaEventRecord(ev[2 * LCDM_HOST_MAX_CHUNKS + 2], stream));
+    chk(cudaStreamWaitEvent(hs->down, ev[2 * LCDM_HOST_MAX_CHUNKS + 2], 0));
+    chk(cudaMemcpyAsync(grad, d.grad, (size_t)B * ncol * sizeof(double), cudaMemcpyDeviceToHost, hs->down));
+    chk(cudaMemcpyAsync(cosmo_status, d.status, (size_t)B * sizeof(int32_t), cudaMemcpyDeviceToHost, hs->down));
+    chk(cudaStreamSynchronize(hs->down));
+    return ok ? LCDM_OK : LCDM_ERR_CUDA;
+}
 
 lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes) {
     if (!opts_ok(opts) || B <= 0 || !bytes) return LCDM_ERR_INVALID;

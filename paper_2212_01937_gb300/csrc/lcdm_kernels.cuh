@@ -99,6 +99,7 @@ struct PairArgs {
     double* grad;            // [B][ncol] accumulated (VJP or d loglike)
     double* loglike;         // [B]
     int64_t chunk;           // pairs per warp (multiple of 32)
+    int64_t base;            // CSR: index of the first pair (z, outputs and offsets are absolute)
 };
 
 template <class T> struct IO;
@@ -330,9 +331,10 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
 #pragma unroll
     for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
     for (int64_t base = start; base < end; base += 32) {
-        const int64_t pidx = base + lane;
-        const bool active = pidx < end;
-        const int64_t pp = active ? pidx : end - 1;
+        const int64_t lidx = base + lane;
+        const bool active = lidx < end;
+        const int64_t pidx = a.base + lidx;                  // absolute pair index
+        const int64_t pp = a.base + (active ? lidx : end - 1);
         int64_t zi = pp;
         if (a.layout == LAYOUT_CSR) {
             if (row < 0) {

@@ -49,13 +49,16 @@ def load():
     lib.lcdm_distances_vjp.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp]
     lib.lcdm_gauss_loglike.argtypes = [_vp, i64, _vp, _vp, _vp, i64, dbl, dbl, _vp, _vp, _vp, _vp, op, _vp,
                                        sz, _vp]
+    lib.lcdm_host_workspace_size.argtypes = [i64, i64, op, ctypes.POINTER(sz)]
+    lib.lcdm_distances_vjp_host.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, i32, _vp]
     lib.lcdm_autotune.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp,
                                   ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
     lib.lcdm_status_string.argtypes = [ctypes.c_int]
     lib.lcdm_status_string.restype = ctypes.c_char_p
     lib.lcdm_launch_count.restype = i64
     for f in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
-              "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune"):
+              "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_host_workspace_size",
+              "lcdm_distances_vjp_host"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -188,6 +191,44 @@ def distances_vjp(params, z, cot, offsets=None, outputs=(), call=None, **kw):
     out["grad"] = grad
     out["status"] = c.status
     return out
+
+
+class HostVJP:
+    """lcdm_distances_vjp_host: the fused forward + adjoint on host arrays,
+    with chunked copies overlapping the kernels.  Inputs and the output arrays
+    are CPU tensors (page-locked for overlap); the device workspace and the
+    output buffers are allocated once here and reused by every call."""
+
+    def __init__(self, B, n, outputs=("d_C", "t", "X", "mu"), ncol=4, precision="fp32", nchunks=4,
+                 device="cuda", block=0, blocks_per_sm=0):
+        lib = load()
+        self.device = torch.device(device)
+        self.opts = Opts(ncol, PRECISION[precision], LAYOUT["csr"], block, blocks_per_sm)
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.B, self.n, self.nchunks = int(B), int(n), int(nchunks)
+        nbytes = ctypes.c_size_t()
+        _check(lib.lcdm_host_workspace_size(self.B, self.n, ctypes.byref(self.opts), ctypes.byref(nbytes)))
+        self.ws = torch.empty(nbytes.value, dtype=torch.uint8, device=self.device)
+        self.outputs = tuple(outputs)
+        self.out = {o: torch.empty(self.n, dtype=self.dtype, pin_memory=True) for o in self.outputs}
+        self.grad = torch.empty(self.B, ncol, dtype=torch.float64, pin_memory=True)
+        self.status = torch.empty(self.B, dtype=torch.int32, pin_memory=True)
+
+    def __call__(self, params, z, cot, offsets):
+        """params [B, ncol] float64, z [n], cot {name: [n]}, offsets [B+1] int64:
+        CPU tensors.  Returns the (reused) host result tensors."""
+        for t in (params, z, offsets, *cot.values()):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError("host entry point: contiguous CPU tensors expected")
+        cp = _VP6(*[(cot[o].data_ptr() if o in cot else None) for o in OUTS])
+        op = _VP6(*[(self.out[o].data_ptr() if o in self.out else None) for o in OUTS])
+        _check(load().lcdm_distances_vjp_host(_ptr(params), self.B, _ptr(offsets), _ptr(z), self.n, cp, op,
+                                              _ptr(self.grad), _ptr(self.status), ctypes.byref(self.opts),
+                                              _ptr(self.ws), self.ws.numel(), self.nchunks, _stream(self.device)))
+        res = dict(self.out)
+        res["grad"] = self.grad
+        res["status"] = self.status
+        return res
 
 
 def gauss_loglike(params, z, m_obs, offsets=None, M=-19.3, sigma=0.1, grad=True, want_mu=False,
