@@ -29,7 +29,10 @@ OUTPUTS = ("d_C", "t", "X", "mu")
 # Work of the dominant kernel per pair for this workload: FP32 floating-point
 # operations (FFMA counted as 2, FADD and FMUL as 1) executed per pair, from
 # the ncu capture summarised in profiles/pairs_kernel_fp32_vjp_4096x1024.md.
-FLOP_PER_PAIR = 6534.1
+FLOP_PER_PAIR = 7246.0
+# DRAM bytes (read + write) per launch of that kernel from the same capture
+# (None once the kernel has changed since the counters were taken).
+TRAFFIC_BYTES = None
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
@@ -211,7 +214,8 @@ def main():
     z_h = z.cpu().pin_memory()
     cot_h = {n: v.cpu().pin_memory() for n, v in cot.items()}
     host = lcdm.HostVJP(B, npairs, outputs=OUTPUTS, precision="fp32", nchunks=8, device=dev,
-                        block=(tune or {}).get("block", 0), blocks_per_sm=(tune or {}).get("blocks_per_sm", 0))
+                        block=(tune or {}).get("block", 0), blocks_per_sm=(tune or {}).get("blocks_per_sm", 0),
+                        lane_map=(tune or {}).get("lane_map", "tuned"))
     h2d = p_h.numel() * 8 + off_h.numel() * 8 + z_h.numel() * 4 + sum(v.numel() * 4 for v in cot_h.values())
     d2h = sum(host.out[n].numel() * 4 for n in OUTPUTS) + host.grad.numel() * 8 + host.status.numel() * 4
 
@@ -233,7 +237,7 @@ def main():
         clocks = clock_summary(rows, local)
         achieved = None if FLOP_PER_PAIR is None else FLOP_PER_PAIR * npairs / (pair_ms / 1e3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
                 "kernel": "pairs_kernel<FP32,K=3,t,X>", "kernel_ms": pair_ms, "prep_ms": prep_ms,
                 "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, nominal clock)"}
         extra = {}

@@ -88,7 +88,17 @@ typedef struct {
     int32_t layout;         /* LCDM_LAYOUT_*                                     */
     int32_t block;          /* threads per block (multiple of 32, <= 256); 0 = tuned */
     int32_t blocks_per_sm;  /* persistent blocks per SM; 0 = tuned               */
+    int32_t lane_map;       /* pairs of a warp's range to lanes: LCDM_MAP_*      */
 } lcdm_opts;
+
+/* lane_map: LCDM_MAP_TUNED takes the autotuner's choice for this workload
+ * class, contiguous until it has run; LCDM_MAP_CONTIGUOUS gives the 32 lanes
+ * 32 consecutive pairs per step (coalesced, best for unordered redshifts);
+ * LCDM_MAP_INTERLEAVED gives lane l the l-th 32nd of the warp's range, so
+ * that every warp sees the whole spread of z even when z is sorted within
+ * the rows (every warp then runs the same code paths, which the instruction
+ * cache needs). */
+enum { LCDM_MAP_TUNED = 0, LCDM_MAP_CONTIGUOUS = 1, LCDM_MAP_INTERLEAVED = 2 };
 
 /* Workspace bytes needed for B cosmologies (per-cosmology root records). */
 lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes);
@@ -193,16 +203,17 @@ lcdm_status lcdm_distances_static(const double* params, int64_t B, const int64_t
                                   const lcdm_opts* opts, cudaStream_t stream);
 
 /* Times the candidate launch shapes (threads per block x persistent blocks
- * per SM) of the pair kernel on the given inputs, keeps the fastest in a
- * process-wide cache keyed by (precision, outputs, tangents, layout, log2
- * npairs) and returns it.  Arguments as lcdm_distances_vjp (grad NULL selects
- * a forward-only shape and cot is then ignored; out entries are overwritten).  The call
- * synchronises the stream; do not call it while capturing a CUDA graph.    */
+ * per SM x lane map) of the pair kernel on the given inputs, keeps the
+ * fastest in a process-wide cache keyed by (precision, outputs, tangents,
+ * layout, log2 npairs) and returns it.  Arguments as lcdm_distances_vjp (grad
+ * NULL selects a forward-only shape and cot is then ignored; out entries are
+ * overwritten).  The call synchronises the stream; do not call it while
+ * capturing a CUDA graph.                                                   */
 lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
                           const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT], double* grad,
                           int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
                           cudaStream_t stream, int32_t* best_block, int32_t* best_blocks_per_sm,
-                          float* best_ms);
+                          float* best_ms, int32_t* best_lane_map);
 
 /* Human-readable name of a lcdm_status value (static string). */
 const char* lcdm_status_string(int status);

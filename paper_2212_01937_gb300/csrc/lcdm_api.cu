@@ -25,7 +25,8 @@ size_t ws_bytes_for(int64_t B) {
 bool opts_ok(const lcdm_opts* o) {
     return o && (o->ncol == 4 || o->ncol == 5) && (o->precision == LCDM_FP64 || o->precision == LCDM_FP32_MIXED) &&
            o->layout >= LCDM_LAYOUT_CSR && o->layout <= LCDM_LAYOUT_SHARED && o->block >= 0 && o->block <= 256 &&
-           (o->block % 32) == 0 && o->blocks_per_sm >= 0 && o->blocks_per_sm <= 64;
+           (o->block % 32) == 0 && o->blocks_per_sm >= 0 && o->blocks_per_sm <= 64 && o->lane_map >= LCDM_MAP_TUNED &&
+           o->lane_map <= LCDM_MAP_INTERLEAVED;
 }
 
 struct Carved {
@@ -63,7 +64,8 @@ const PairsTable& table(int prec, int K) {
 
 // tuned launch shapes: key (precision, K, WT, WX, layout, log2 npairs)
 typedef std::tuple<int, int, int, int, int, int> TuneKey;
-std::map<TuneKey, std::pair<int, int> > g_tuned;
+struct Tuned { int block, bps, lane_map; };
+std::map<TuneKey, Tuned> g_tuned;
 std::mutex g_tune_mu;
 
 int log2_bucket(int64_t n) {
@@ -131,17 +133,19 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
     return LCDM_OK;
 }
 
-lcdm_status launch_plan(Plan& P, int block, int bps, cudaStream_t s) {
+lcdm_status launch_plan(Plan& P, int block, int bps, int lane_map, cudaStream_t s) {
     const PairsTable& t = table(P.prec, P.K);
     int idx = (P.wt ? 2 : 0) + (P.wx ? 1 : 0);
-    if (block == 0 || bps == 0) {
+    if (block == 0 || bps == 0 || lane_map == LCDM_MAP_TUNED) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tuned.find(P.key);
         if (it != g_tuned.end()) {
-            if (block == 0) block = it->second.first;
-            if (bps == 0) bps = it->second.second;
+            if (block == 0) block = it->second.block;
+            if (bps == 0) bps = it->second.bps;
+            if (lane_map == LCDM_MAP_TUNED) lane_map = it->second.lane_map;
         }
     }
+    P.args.interleave = lane_map == LCDM_MAP_INTERLEAVED ? 1 : 0;
     if (block == 0) block = 128;
     int occ = t.occ[idx](block);
     if (occ <= 0) return LCDM_ERR_CUDA;
@@ -210,7 +214,7 @@ lcdm_status pairs_common(const double* params, int64_t B, const int64_t* offsets
     make_plan(params, B, offsets, z, n, out, jac, cot, mobs, M, sigma, grad, loglike, status, opts, cv, P);
     st = run_prep(params, B, opts, cv, status, grad, loglike, stream);
     if (st != LCDM_OK) return st;
-    return launch_plan(P, opts->block, opts->blocks_per_sm, stream);
+    return launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
 }
 
 // ----------------------------------------------------------------------------
@@ -397,7 +401,7 @@ lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64
         make_plan(d.params + r0 * ncol, r1 - r0, d.offsets + r0, d.z, o1 - o0, outd, nullptr, cotd, nullptr, 0, 1,
                   d.grad + r0 * ncol, nullptr, d.status + r0, opts, rc, P);
         P.args.base = o0;
-        st = launch_plan(P, opts->block, opts->blocks_per_sm, stream);
+        st = launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
         if (st != LCDM_OK) return st;
         chk(cudaEventRecord(ev[3 + 2 * c], stream));
         chk(cudaStreamWaitEvent(hs->down, ev[3 + 2 * c], 0));
@@ -470,7 +474,8 @@ lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* o
 lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
                           const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT], double* grad,
                           int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
-                          cudaStream_t stream, int32_t* best_block, int32_t* best_bps, float* best_ms) {
+                          cudaStream_t stream, int32_t* best_block, int32_t* best_bps, float* best_ms,
+                          int32_t* best_map) {
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
     if (!grad) cot = nullptr;   // forward-only shape
@@ -485,34 +490,39 @@ lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offset
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return LCDM_ERR_CUDA;
     const int blocks[] = {64, 128, 256};
     float best = 1e30f;
-    int bb = 128, bbps = 1;
-    for (int block : blocks) {
-        int occ = t.occ[idx](block);
-        for (int bps = 1; bps <= occ; bps *= 2) {
-            float tot = 0;
-            for (int rep = 0; rep < 3; rep++) {
-                if (run_prep(params, B, opts, cv, cosmo_status, grad, nullptr, stream) != LCDM_OK) return LCDM_ERR_CUDA;
-                cudaEventRecord(e0, stream);
-                if (launch_plan(P, block, bps, stream) != LCDM_OK) return LCDM_ERR_CUDA;
-                cudaEventRecord(e1, stream);
-                cudaEventSynchronize(e1);
-                float ms = 0;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (rep > 0) tot += ms;
+    int bb = 128, bbps = 1, bmap = LCDM_MAP_CONTIGUOUS;
+    for (int map = LCDM_MAP_CONTIGUOUS; map <= LCDM_MAP_INTERLEAVED; map++) {
+        if (opts->lane_map != LCDM_MAP_TUNED && map != opts->lane_map) continue;
+        for (int block : blocks) {
+            int occ = t.occ[idx](block);
+            for (int bps = 1; bps <= occ; bps *= 2) {
+                float tot = 0;
+                for (int rep = 0; rep < 3; rep++) {
+                    if (run_prep(params, B, opts, cv, cosmo_status, grad, nullptr, stream) != LCDM_OK)
+                        return LCDM_ERR_CUDA;
+                    cudaEventRecord(e0, stream);
+                    if (launch_plan(P, block, bps, map, stream) != LCDM_OK) return LCDM_ERR_CUDA;
+                    cudaEventRecord(e1, stream);
+                    cudaEventSynchronize(e1);
+                    float ms = 0;
+                    cudaEventElapsedTime(&ms, e0, e1);
+                    if (rep > 0) tot += ms;
+                }
+                tot /= 2;
+                if (tot < best) { best = tot; bb = block; bbps = bps; bmap = map; }
             }
-            tot /= 2;
-            if (tot < best) { best = tot; bb = block; bbps = bps; }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[P.key] = std::make_pair(bb, bbps);
+        g_tuned[P.key] = Tuned{bb, bbps, bmap};
     }
     if (best_block) *best_block = bb;
     if (best_bps) *best_bps = bbps;
     if (best_ms) *best_ms = best;
+    if (best_map) *best_map = bmap;
     return cudaGetLastError() == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
 }
 

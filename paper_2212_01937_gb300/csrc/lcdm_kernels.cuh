@@ -100,6 +100,7 @@ struct PairArgs {
     double* loglike;         // [B]
     int64_t chunk;           // pairs per warp (multiple of 32)
     int64_t base;            // CSR: index of the first pair (z, outputs and offsets are absolute)
+    int interleave;          // lane l takes the l-th 32nd of the warp's range (else 32 consecutive pairs)
 };
 
 template <class T> struct IO;
@@ -330,11 +331,13 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
     int64_t acc_row = -1;
 #pragma unroll
     for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
-    for (int64_t base = start; base < end; base += 32) {
-        const int64_t lidx = base + lane;
-        const bool active = lidx < end;
+    const int64_t len = end - start, nb = (len + 31) / 32;
+    for (int64_t it = 0; it < nb; it++) {
+        const int64_t off = a.interleave ? (int64_t)lane * nb + it : it * 32 + lane;
+        const bool active = off < len;
+        const int64_t lidx = start + (active ? off : len - 1);
         const int64_t pidx = a.base + lidx;                  // absolute pair index
-        const int64_t pp = a.base + (active ? lidx : end - 1);
+        const int64_t pp = pidx;
         int64_t zi = pp;
         if (a.layout == LAYOUT_CSR) {
             if (row < 0) {

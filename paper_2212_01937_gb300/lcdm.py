@@ -24,7 +24,10 @@ _lib = None
 
 class Opts(ctypes.Structure):
     _fields_ = [("ncol", ctypes.c_int32), ("precision", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("lane_map", ctypes.c_int32)]
+
+
+LANE_MAP = {"tuned": 0, "contiguous": 1, "interleaved": 2}
 
 
 _vp = ctypes.c_void_p
@@ -52,7 +55,8 @@ def load():
     lib.lcdm_host_workspace_size.argtypes = [i64, i64, op, ctypes.POINTER(sz)]
     lib.lcdm_distances_vjp_host.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, i32, _vp]
     lib.lcdm_autotune.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp,
-                                  ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float)]
+                                  ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
+                                  ctypes.POINTER(i32)]
     lib.lcdm_status_string.argtypes = [ctypes.c_int]
     lib.lcdm_status_string.restype = ctypes.c_char_p
     lib.lcdm_launch_count.restype = i64
@@ -85,7 +89,7 @@ class Call:
     """Prepared arguments of one batch (validated and placed on the device)."""
 
     def __init__(self, params, z, offsets=None, layout=None, precision="fp32", block=0, blocks_per_sm=0,
-                 workspace=None):
+                 workspace=None, lane_map="tuned"):
         lib = load()
         if not params.is_cuda:
             raise ValueError("params must be a CUDA tensor")
@@ -113,7 +117,7 @@ class Call:
         else:
             self.n = self.z.numel()
             self.npairs = self.B * self.n
-        self.opts = Opts(ncol, PRECISION[precision], LAYOUT[layout], block, blocks_per_sm)
+        self.opts = Opts(ncol, PRECISION[precision], LAYOUT[layout], block, blocks_per_sm, LANE_MAP[lane_map])
         nbytes = ctypes.c_size_t()
         _check(lib.lcdm_workspace_size(self.B, ctypes.byref(self.opts), ctypes.byref(nbytes)))
         if workspace is not None and workspace.numel() >= nbytes.value:
@@ -200,10 +204,10 @@ class HostVJP:
     output buffers are allocated once here and reused by every call."""
 
     def __init__(self, B, n, outputs=("d_C", "t", "X", "mu"), ncol=4, precision="fp32", nchunks=4,
-                 device="cuda", block=0, blocks_per_sm=0):
+                 device="cuda", block=0, blocks_per_sm=0, lane_map="tuned"):
         lib = load()
         self.device = torch.device(device)
-        self.opts = Opts(ncol, PRECISION[precision], LAYOUT["csr"], block, blocks_per_sm)
+        self.opts = Opts(ncol, PRECISION[precision], LAYOUT["csr"], block, blocks_per_sm, LANE_MAP[lane_map])
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.B, self.n, self.nchunks = int(B), int(n), int(nchunks)
         nbytes = ctypes.c_size_t()
@@ -259,10 +263,11 @@ def autotune(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), cot=None,
         cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items()}
         cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])
         grad = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device)
-    bb, bbps, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+    bb, bbps, ms, bm = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float(), ctypes.c_int32()
     _check(load().lcdm_autotune(*c.common(), cp, vp, _ptr(grad), _ptr(c.status), *c.tail(), ctypes.byref(bb),
-                                ctypes.byref(bbps), ctypes.byref(ms)))
-    return {"block": bb.value, "blocks_per_sm": bbps.value, "ms": ms.value}
+                                ctypes.byref(bbps), ctypes.byref(ms), ctypes.byref(bm)))
+    names = {v: k for k, v in LANE_MAP.items()}
+    return {"block": bb.value, "blocks_per_sm": bbps.value, "ms": ms.value, "lane_map": names[bm.value]}
 
 
 class Distances(torch.autograd.Function):

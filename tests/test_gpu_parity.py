@@ -369,3 +369,21 @@ def test_stress_sampled_vs_carlson_oracle(lib):
         ref = oracle.carlson_distances(s.params[rows], zin[idx].astype(np.float64), np.arange(idx.size + 1))
         sub = {n: res[n][torch.tensor(idx, device=DEV)] for n in ("d_C", "t", "X", "mu")}
         _check(sub, ref, tol, prec, cosmo, names=("d_C", "t", "X"), mu_lim=mu_lim)
+
+
+def test_lane_maps_agree_on_sorted_redshifts(lib):
+    """Contiguous and interleaved lane maps give the same per-pair outputs and
+    the same gradients (FP64 sums, order aside); the autotuner reports one."""
+    b = workloads.config2(B=24, n=300, seed=14)
+    z = np.sort(b.z.reshape(b.B, -1), axis=1).reshape(-1).astype(np.float32)
+    g = np.random.default_rng(2).normal(size=z.size).astype(np.float32)
+    p, zt, off = _t(b.params), _t(z), _t(b.offsets)
+    cot = {n: _t(g) for n in ("d_C", "t", "X", "mu")}
+    res = {m: lib.distances_vjp(p, zt, cot, off, outputs=("d_C", "t", "X", "mu"), precision="fp32", lane_map=m)
+           for m in ("contiguous", "interleaved")}
+    torch.cuda.synchronize()
+    for n in ("d_C", "t", "X", "mu"):
+        assert torch.equal(res["contiguous"][n], res["interleaved"][n]), n
+    assert torch.allclose(res["contiguous"]["grad"], res["interleaved"]["grad"], rtol=1e-12, atol=1e-12)
+    t = lib.autotune(p, zt, off, outputs=("d_C", "t", "X", "mu"), cot=cot)
+    assert t["lane_map"] in ("contiguous", "interleaved")
