@@ -38,7 +38,7 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x ma
 
 def workload(seed_offset=0):
     from paper_2212_01937_gb300 import workloads
-    b = workloads.config2(seed=2 + seed_offset)
+    b = workloads.general_batch(seed=2 + seed_offset)
     return b
 
 
@@ -252,7 +252,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": b.name + " (configs[1]: general LCDM+radiation+curvature batch)",
+                "config": {"workload": b.name + " (general LCDM+radiation+curvature batch: 4096 cosmologies x 1024 z)",
                            "B": B, "n_per_row": 1024, "pairs_per_gpu": npairs, "outputs": list(OUTPUTS),
                            "gradient": "fused VJP w.r.t. (H0, Om, OL, Or), random cotangents on all outputs",
                            "precision": "FP32 per-pair arithmetic, FP64 root preparation and reductions",
@@ -301,7 +301,7 @@ def vi_step_rate(dev, steps=10):
     gradient, Adam), replayed from its CUDA graph."""
     import torch
     from paper_2212_01937_gb300 import vi, workloads
-    d = workloads.config3()
+    d = workloads.supernovae()
     centre, scale = vi.default_guide(d.extra["truth"])
     opt = vi.GaussianVI(torch.tensor(d.z, dtype=torch.float32, device=dev), torch.tensor(d.m_obs, device=dev),
                         centre, scale, M=d.M, sigma=d.sigma, samples=256)
@@ -315,7 +315,7 @@ def vi_step_rate(dev, steps=10):
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
-    return {"workload": d.name + " x 256 guide samples (configs[2]), FP32, CUDA-graph replay",
+    return {"workload": d.name + " x 256 guide samples (10^6 mock SNe Ia, shared z), FP32, CUDA-graph replay",
             "ms_per_step": ms, "pairs_per_step": opt.pairs_per_step,
             "value": opt.pairs_per_step / (ms / 1e3), "unit": UNIT}
 

@@ -332,8 +332,9 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
 #pragma unroll
     for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
     const int64_t len = end - start, nb = (len + 31) / 32;
+    const int64_t s_lane = a.interleave ? nb : 1, s_it = a.interleave ? 1 : 32;
     for (int64_t it = 0; it < nb; it++) {
-        const int64_t off = a.interleave ? (int64_t)lane * nb + it : it * 32 + lane;
+        const int64_t off = (int64_t)lane * s_lane + it * s_it;
         const bool active = off < len;
         const int64_t lidx = start + (active ? off : len - 1);
         const int64_t pidx = a.base + lidx;                  // absolute pair index

@@ -108,7 +108,7 @@ def _draw_cosmo(rng, Om_rng=(0.05, 0.6), OL_rng=(0.0, 1.2), lOr_rng=(-5.0, -4.0)
             return H0, Om, OL, Or
 
 
-def config1(n=10_000, seed=0):
+def flat_radiationless(n=10_000, seed=0):
     """One flat radiationless cosmology (70, 0.3, 0.7, 0); z ~ U(0.01, 2)."""
     rng = np.random.default_rng(seed)
     params = np.array([[70.0, 0.3, 0.7, 0.0]])
@@ -116,7 +116,7 @@ def config1(n=10_000, seed=0):
     return Batch("flat-radiationless-1x%d" % n, params, z, np.array([0, n], dtype=np.int64))
 
 
-def config2(B=4096, n=1024, seed=2, zmax=10.0):
+def general_batch(B=4096, n=1024, seed=2, zmax=10.0):
     """General LCDM+radiation+curvature batch: Om ~ U(.05,.6), OL ~ U(0,1.2),
     Or ~ logU(1e-5,1e-4), H0 ~ U(60,80), n redshifts each z ~ U(0, zmax)."""
     rng = np.random.default_rng(seed)
@@ -130,7 +130,7 @@ def config2(B=4096, n=1024, seed=2, zmax=10.0):
                  np.arange(B + 1, dtype=np.int64) * n)
 
 
-def config3(N=1_000_000, seed=1, truth=(70.0, 0.3, 0.7, 5e-5), M=-19.3, sigma=0.1):
+def supernovae(N=1_000_000, seed=1, truth=(70.0, 0.3, 0.7, 5e-5), M=-19.3, sigma=0.1):
     """N mock SNe Ia: z ~ U(0.01, 1.5), m_obs = mu_mock(z; truth) + M + N(0, sigma^2).
     The stand-in for the Sec. 4 mock sets (up to 10^6 SNe)."""
     rng = np.random.default_rng(seed)
@@ -141,8 +141,8 @@ def config3(N=1_000_000, seed=1, truth=(70.0, 0.3, 0.7, 5e-5), M=-19.3, sigma=0.
                  m_obs=m_obs, M=M, sigma=sigma, extra={"truth": truth})
 
 
-def config4(B=16384, seed=3, nmax_exp=5.0, M=-19.3, sigma=0.1):
-    """Ragged batch: cosmologies as config2; row length floor(10^U(0, nmax_exp));
+def ragged_batch(B=16384, seed=3, nmax_exp=5.0, M=-19.3, sigma=0.1):
+    """Ragged batch: cosmologies as general_batch; row length floor(10^U(0, nmax_exp));
     z ~ U(0, 3); per-row mock magnitudes from the row's own cosmology."""
     rng = np.random.default_rng(seed)
     params = np.zeros((B, 4))
@@ -163,7 +163,7 @@ def config4(B=16384, seed=3, nmax_exp=5.0, M=-19.3, sigma=0.1):
                  m_obs=np.concatenate(ms), M=M, sigma=sigma)
 
 
-def config5(B=10_000, n=10_000, seed=4):
+def precision_stress(B=10_000, n=10_000, seed=4):
     """Precision stress: half the cosmologies within 1e-6 of flatness
     (Ok ~ U(-1e-6, 1e-6), OL = 1 - Om - Or - Ok), half just inside the
     no-Big-Bang boundary (OL = OL_crit(Om, Or) (1 - delta), delta ~ U(0, 1e-6));

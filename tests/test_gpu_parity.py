@@ -34,7 +34,7 @@ def _t(a, dtype=None):
 
 def _batch_small():
     """Several tiles per row and a ragged tail: 24 rows of varying length."""
-    b = workloads.config2(B=24, n=1, seed=11)
+    b = workloads.general_batch(B=24, n=1, seed=11)
     rng = np.random.default_rng(11)
     lens = rng.integers(1, 300, b.B)
     lens[3] = 0
@@ -91,7 +91,7 @@ def _check(res, ref, tol, prec, cosmo, names=("d_C", "t", "X", "d_M", "d_L"), mu
 
 
 def test_roots_match_oracle(lib):
-    P = np.vstack([workloads.config2(B=30, n=1, seed=4).params,
+    P = np.vstack([workloads.general_batch(B=30, n=1, seed=4).params,
                    [[70, 0.3, 0.7, 0.0], [70, 0.3, 0.7, 1e-5], [60, 0.05, 0.2, 0.0], [70, 0.2, 0.06, 2.4e-5]]])
     r = lib.roots(_t(P))
     torch.cuda.synchronize()
@@ -129,7 +129,7 @@ def test_forward_csr_vs_quadrature(lib, prec):
 
 
 def test_config1_flat_radiationless(lib):
-    b = workloads.config1()
+    b = workloads.flat_radiationless()
     ref = oracle.quad_distances(b.params, b.z, b.offsets)
     res = lib.distances(_t(b.params), _t(b.z), _t(b.offsets), outputs=("d_C", "mu"), precision="fp64")
     torch.cuda.synchronize()
@@ -137,7 +137,7 @@ def test_config1_flat_radiationless(lib):
 
 
 def test_layouts_agree(lib):
-    b = workloads.config2(B=9, n=70, seed=8)
+    b = workloads.general_batch(B=9, n=70, seed=8)
     p = _t(b.params)
     z = _t(b.z.astype(np.float32))
     dense = lib.distances(p, z, None, layout="dense", outputs=("d_C", "mu"))
@@ -151,7 +151,7 @@ def test_layouts_agree(lib):
 
 
 def test_stress_near_flat_and_near_boundary(lib):
-    s = workloads.config5(B=8, n=40, seed=4)
+    s = workloads.precision_stress(B=8, n=40, seed=4)
     ref = oracle.quad_distances(s.params, s.z, s.offsets)
     r64 = lib.distances(_t(s.params), _t(s.z), _t(s.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp64")
     z32 = s.z.astype(np.float32)
@@ -168,7 +168,7 @@ def test_stress_near_flat_and_near_boundary(lib):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_jacobian_vs_leibniz_oracle(lib, prec):
-    b = workloads.config2(B=6, n=33, seed=9)
+    b = workloads.general_batch(B=6, n=33, seed=9)
     z = b.z.copy()
     z[:66:11] = [1e-4, 1e-3, 1e-2, 0.1, 30.0, 1100.0]
     zin = z if prec == "fp64" else z.astype(np.float32)
@@ -188,7 +188,7 @@ def test_jacobian_vs_leibniz_oracle(lib, prec):
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32"])
 def test_vjp_matches_jacobian_and_oracle(lib, prec):
-    b = workloads.config2(B=7, n=45, seed=10)
+    b = workloads.general_batch(B=7, n=45, seed=10)
     dt = np.float64 if prec == "fp64" else np.float32
     rng = np.random.default_rng(1)
     cot = {n: rng.normal(size=b.nnz).astype(dt) for n in ("d_C", "t", "X", "mu")}
@@ -219,7 +219,7 @@ def test_fp64_gradients_vs_central_differences(lib):
     (truncation about 4 (h/theta)^4 relative) and a smaller step leaves only
     rounding noise at low z.  The bound adds that noise, 1.5 x 8 ulp(f) / h
     (the coefficients' absolute sum is 18/12)."""
-    b = workloads.config2(B=3, n=8, seed=12)
+    b = workloads.general_batch(B=3, n=8, seed=12)
     z = b.z.copy()
     z[:4] = [1e-3, 0.05, 200.0, 1100.0]
     outs = ("d_C", "t", "X", "mu")
@@ -250,7 +250,7 @@ def test_fp64_gradients_vs_central_differences(lib):
 
 
 def test_gauss_loglike_vs_oracle(lib):
-    b = workloads.config4(B=20, seed=3, nmax_exp=2.5)
+    b = workloads.ragged_batch(B=20, seed=3, nmax_exp=2.5)
     for prec in ("fp64", "fp32"):
         dt = np.float64 if prec == "fp64" else np.float32
         zin, m = b.z.astype(dt), b.m_obs.astype(dt)
@@ -286,9 +286,9 @@ def test_status_codes_and_nan_outputs(lib):
 
 
 def test_full_size_sampled_bench_configuration(lib):
-    """config2 at full size (4096 x 1024) in the benchmark's launch shape, a
+    """general_batch at full size (4096 x 1024) in the benchmark's launch shape, a
     random sample checked pair by pair against the Carlson oracle."""
-    b = workloads.config2()
+    b = workloads.general_batch()
     z32 = b.z.astype(np.float32)
     res = lib.distances(_t(b.params), _t(z32), _t(b.offsets), outputs=("d_C", "t", "X", "mu"), precision="fp32")
     torch.cuda.synchronize()
@@ -304,7 +304,7 @@ def test_full_size_sampled_bench_configuration(lib):
 
 
 def test_autotune_and_launch_count(lib):
-    b = workloads.config2(B=64, n=256, seed=3)
+    b = workloads.general_batch(B=64, n=256, seed=3)
     n0 = lib.launch_count()
     t = lib.autotune(_t(b.params), _t(b.z.astype(np.float32)), _t(b.offsets), outputs=("d_C", "mu"))
     assert t["block"] in (64, 128, 256) and t["blocks_per_sm"] >= 1 and t["ms"] > 0
@@ -316,7 +316,7 @@ def test_ragged_loglike_step_in_cuda_graph(lib):
     lengths logU(1, 10^3), empty rows included) captured in a CUDA graph:
     replays reproduce the eager call, and new parameters copied into the
     captured buffer are picked up by the replay."""
-    b = workloads.config4(B=96, seed=3, nmax_exp=3.0)
+    b = workloads.ragged_batch(B=96, seed=3, nmax_exp=3.0)
     dev = torch.device(DEV)
     params = _t(b.params)
     z, m, off = _t(b.z.astype(np.float32)), _t(b.m_obs.astype(np.float32)), _t(b.offsets)
@@ -355,7 +355,7 @@ def test_stress_sampled_vs_carlson_oracle(lib):
     the integrand has a peak of relative width ~ sqrt(delta) ~ 1e-3 set by the
     near-double root; rounding the roots to FP32 moves it by ~1e-7 relative,
     so FP32 d_C and t are stated to 3e-5 here (measured 1.7e-5)."""
-    s = workloads.config5(B=64, n=2000, seed=4)
+    s = workloads.precision_stress(B=64, n=2000, seed=4)
     rng = np.random.default_rng(1)
     idx = np.sort(rng.choice(s.nnz, 4000, replace=False))
     rows = np.searchsorted(s.offsets, idx, side="right") - 1
@@ -374,7 +374,7 @@ def test_stress_sampled_vs_carlson_oracle(lib):
 def test_lane_maps_agree_on_sorted_redshifts(lib):
     """Contiguous and interleaved lane maps give the same per-pair outputs and
     the same gradients (FP64 sums, order aside); the autotuner reports one."""
-    b = workloads.config2(B=24, n=300, seed=14)
+    b = workloads.general_batch(B=24, n=300, seed=14)
     z = np.sort(b.z.reshape(b.B, -1), axis=1).reshape(-1).astype(np.float32)
     g = np.random.default_rng(2).normal(size=z.size).astype(np.float32)
     p, zt, off = _t(b.params), _t(z), _t(b.offsets)

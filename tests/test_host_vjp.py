@@ -14,7 +14,7 @@ OUTS = ("d_C", "t", "X", "mu")
 
 
 def _ragged(seed=3):
-    b = workloads.config4(B=40, seed=seed, nmax_exp=2.5)
+    b = workloads.ragged_batch(B=40, seed=seed, nmax_exp=2.5)
     return b
 
 

@@ -76,7 +76,7 @@ def test_simpson_brute_force():
 
 
 def _config2_small(B=24, n=16, seed=21):
-    return workloads.config2(B=B, n=n, seed=seed)
+    return workloads.general_batch(B=B, n=n, seed=seed)
 
 
 def test_carlson_vs_quadrature_random():
@@ -208,7 +208,7 @@ def test_near_boundary_peak_resolved():
 
 
 def test_stress_rows_quadrature_vs_carlson():
-    s = workloads.config5(B=6, n=25, seed=4)
+    s = workloads.precision_stress(B=6, n=25, seed=4)
     o1 = q(s.params, s.z, offsets=s.offsets)
     o2 = oracle.carlson_distances(s.params, s.z, offsets=s.offsets)
     assert rel(o2[:, :2], o1[:, :2]) < 1e-9

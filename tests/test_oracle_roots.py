@@ -7,7 +7,7 @@ from paper_2212_01937_gb300 import workloads
 
 
 def _batch():
-    b = workloads.config2(B=40, n=1, seed=7)
+    b = workloads.general_batch(B=40, n=1, seed=7)
     extra = np.array([[70, 0.3, 0.7, 0.0], [70, 0.3, 0.7, 1e-5], [60, 0.05, 0.2, 0.0],
                       [70, 0.6, 1.1, 5e-5], [70, 0.2, 0.06, 2.4e-5]])
     return np.vstack([b.params, extra])

@@ -5,21 +5,21 @@ from paper_2212_01937_gb300 import workloads
 
 
 def test_config_shapes_and_seeds():
-    b = workloads.config2(B=8, n=5, seed=2)
+    b = workloads.general_batch(B=8, n=5, seed=2)
     assert b.params.shape == (8, 4) and b.z.shape == (40,) and b.offsets[-1] == 40
-    b2 = workloads.config2(B=8, n=5, seed=2)
+    b2 = workloads.general_batch(B=8, n=5, seed=2)
     assert np.array_equal(b.params, b2.params) and np.array_equal(b.z, b2.z)
     assert np.all((b.params[:, 1] >= 0.05) & (b.params[:, 1] <= 0.6))
     assert np.all((b.params[:, 3] >= 1e-5) & (b.params[:, 3] <= 1e-4))
-    r = workloads.config4(B=50, seed=3, nmax_exp=3.0)
+    r = workloads.ragged_batch(B=50, seed=3, nmax_exp=3.0)
     assert r.offsets[0] == 0 and r.offsets[-1] == r.nnz and np.all(np.diff(r.offsets) >= 1)
     assert r.m_obs.shape == r.z.shape
-    c1 = workloads.config1(n=100)
+    c1 = workloads.flat_radiationless(n=100)
     assert c1.params.tolist() == [[70.0, 0.3, 0.7, 0.0]]
 
 
 def test_stress_config_near_boundaries():
-    s = workloads.config5(B=4, n=3, seed=4)
+    s = workloads.precision_stress(B=4, n=3, seed=4)
     assert s.params.shape == (4, 5)
     assert np.all(np.abs(s.params[0::2, 4]) <= 1e-6 + 1e-15)
     for Om, OL, Or, Ok in s.params[1::2, 1:5]:

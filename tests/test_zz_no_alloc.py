@@ -22,7 +22,7 @@ def test_static_entry_matches_workspace_entry():
     fn.restype = ctypes.c_int
     dev = torch.device("cuda:0")
     for seed, prec in ((21, "fp32"), (22, "fp64")):
-        b = workloads.config2(B=40, n=77, seed=seed)
+        b = workloads.general_batch(B=40, n=77, seed=seed)
         dt = torch.float32 if prec == "fp32" else torch.float64
         params = torch.tensor(b.params, device=dev)
         z = torch.tensor(b.z, dtype=dt, device=dev)
