@@ -524,6 +524,7 @@ LCDM_HD int even_exponent(float mag) {
 // and the final series) so that close p and x1 cause no cancellation.
 template <class T, int NJ, bool WANT_D, class PT, bool DDL = false, bool WANT_DP = WANT_D>
 LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T hl = T()) {
+    static_assert(!DDL || (WANT_D && NJ > 0), "the divided-difference track needs R_D and an R_J track");
     DupResult<T, NJ, PT> R;
     float mag = fabsf((float)sval(x1));
     float pm = pmag(pr);
@@ -583,7 +584,8 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
             T d = (sq + s1) * pprod(padd(sp, sq));
             T f3 = f * f * f;
             T ee = f3 * delta[j] / (d * d);
-            sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
+            // the divided-difference track's own R_J follows from R_D and DJ
+            if (!(DDL && j == NJ - 1)) sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
             if (DDL && j == NJ - 1) {
                 // [R_C(1,1+e)/d_p - 1/d_x1] / h with e/h = f^3 Pi / d_p^2 and
                 // (d_p - d_x1)/h = f [g(a) + 2b (a + b + sum sqrt(pair))] / (a + b),
@@ -622,7 +624,7 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
     if (WANT_DP) R.RDp = pldexp(rd_pair_series(x1, pr, f, sDp), -3 * e / 2);
     else R.RDp = pzero(pr);
 #pragma unroll
-    for (int j = 0; j < NJ; j++) {
+    for (int j = 0; j < (DDL ? NJ - 1 : NJ); j++) {
         T A = (x1 + psum(pr) + cst<T>(2.0) * p[j]) * cst<T>(0.2), iA = cst<T>(1.0) / A;
         T X = (A - x1) * iA, P = (A - p[j]) * iA;
         PT Y = pscale(prsub(A, pr), iA);
@@ -652,6 +654,8 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         // R_J(p) - R_D = f (T(u1) - T(u2)) + 6 (sum_p - sum_x1), T = A^-3/2 S,
         // with u1 - u2 = f hs and the sums' difference = hs sDD
         R.DJ = sldexp(f * f * dser + cst<T>(6.0) * sDD, -5 * e / 2);
+        // R_J(x1 + hl) = R_D(x2, x3, x1) + hl DJ: a sum, no cancellation
+        R.RJ[NJ - 1] = R.RD1 + hl * R.DJ;
     }
     return R;
 }
