@@ -191,12 +191,7 @@ def main():
     th.join(timeout=10)
     launches = lcdm.launch_count() - launches0
     ms = sum(e0.elapsed_time(e1) for e0, e1 in ev) / args.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = npairs * world / (ms / 1e3)
+    ms, value = aggregate(ms, npairs, world, dist, dev)
 
     # device time of the pair kernel alone: CUDA-graph replays of (L2 flush + step)
     # minus replays of (L2 flush + root preparation), so host overheads drop out
@@ -230,7 +225,7 @@ def main():
         e2e_step()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    e2e_value = npairs * world / (e2e_ms / 1e3)
+    e2e_ms, e2e_value = aggregate(e2e_ms, npairs, world, dist, dev)
 
     line = None
     if rank == 0:
@@ -269,6 +264,19 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def aggregate(ms, npairs, world, dist=None, device=None):
+    """Whole-job figures under weak scaling: every rank times its own batch of
+    npairs; the job's step time is the slowest rank's (max over ranks, after a
+    barrier) and its rate is all ranks' pairs over that time."""
+    import torch
+    if dist is not None and dist.is_initialized():
+        t = torch.tensor([ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    return ms, npairs * world / (ms / 1e3)
 
 
 def graph_ms(fn, dev, reps=10):
