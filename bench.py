@@ -134,6 +134,7 @@ def main():
     ap.add_argument("--no-fp64-baseline", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--no-vi", action="store_true", help="skip the variational-inference step timing")
+    ap.add_argument("--no-ragged", action="store_true", help="skip the ragged log-likelihood step timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -260,6 +261,8 @@ def main():
         line.update(extra)
         if not args.no_vi:
             line["vi_step"] = vi_step_rate(dev)
+        if not args.no_ragged:
+            line["ragged_step"] = ragged_step_rate(dev)
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -326,6 +329,23 @@ def vi_step_rate(dev, steps=10):
     return {"workload": d.name + " x 256 guide samples (10^6 mock SNe Ia, shared z), FP32, CUDA-graph replay",
             "ms_per_step": ms, "pairs_per_step": opt.pairs_per_step,
             "value": opt.pairs_per_step / (ms / 1e3), "unit": UNIT}
+
+
+def ragged_step_rate(dev, steps=10):
+    """One log-likelihood + gradient step over the ragged batch (16384
+    cosmologies, floor(10^U(0, 5)) redshifts each, about 1.46e8 pairs in CSR
+    layout, per-row mock magnitudes), replayed from a CUDA graph."""
+    import torch
+    from paper_2212_01937_gb300 import lcdm, workloads
+    d = workloads.ragged_batch()
+    params = torch.tensor(d.params, device=dev)
+    off = torch.tensor(d.offsets, device=dev)
+    z = torch.tensor(d.z, dtype=torch.float32).to(dev)
+    m = torch.tensor(d.m_obs, dtype=torch.float32).to(dev)
+    call = lcdm.Call(params, z, off, precision="fp32")
+    ms = graph_ms(lambda: lcdm.gauss_loglike(params, z, m, off, M=d.M, sigma=d.sigma, call=call), dev, reps=steps)
+    return {"workload": d.name + " (16384 cosmologies x floor(10^U(0,5)) z, CSR), FP32, CUDA-graph replay",
+            "pairs_per_step": int(d.nnz), "ms_per_step": ms, "value": d.nnz / (ms / 1e3), "unit": UNIT}
 
 
 def fp64_baselines(lcdm, params, offsets, b, dev):
