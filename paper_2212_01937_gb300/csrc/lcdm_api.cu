@@ -146,7 +146,7 @@ lcdm_status launch_plan(Plan& P, int block, int bps, int lane_map, cudaStream_t 
         }
     }
     P.args.interleave = lane_map == LCDM_MAP_INTERLEAVED ? 1 : 0;
-    if (block == 0) block = 128;
+    if (block == 0) block = 256;   // one full-SM block per SM, warps in lockstep (see pairs_kernel)
     int occ = t.occ[idx](block);
     if (occ <= 0) return LCDM_ERR_CUDA;
     if (bps == 0 || bps > occ) bps = occ;

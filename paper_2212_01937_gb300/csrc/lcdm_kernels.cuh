@@ -319,8 +319,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t start = warp * a.chunk;
-    if (start >= a.nnz) return;
-    const int64_t end = min(start + a.chunk, a.nnz);
+    const int64_t end = max(start, min(start + a.chunk, a.nnz));   // empty range past the end
     const bool reduce = (a.grad != nullptr) || (a.loglike != nullptr);
     const bool loglike = a.mobs != nullptr;
     const TO inv_sig = (TO)(1.0 / a.sigma);
@@ -331,9 +330,16 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
     int64_t acc_row = -1;
 #pragma unroll
     for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
-    const int64_t len = end - start, nb = (len + 31) / 32;
+    const int64_t len = end - start, nb = (len + 31) / 32, nb_all = a.chunk / 32;
     const int64_t s_lane = a.interleave ? nb : 1, s_it = a.interleave ? 1 : 32;
-    for (int64_t it = 0; it < nb; it++) {
+    // With a full-SM block (256 threads, one block per SM) the warps step through
+    // their ranges together, one 32-pair batch at a time: the fused code of a pair
+    // is about the size of the instruction cache, and warps at the same place in
+    // it share each fetched line.  Every warp runs nb_all steps (the same number).
+    const bool lockstep = blockDim.x == 256;
+    for (int64_t it = 0; it < nb_all; it++) {
+        if (lockstep) __syncthreads();
+        if (it >= nb) continue;
         const int64_t off = (int64_t)lane * s_lane + it * s_it;
         const bool active = off < len;
         const int64_t lidx = start + (active ? off : len - 1);
