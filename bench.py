@@ -36,6 +36,13 @@ TRAFFIC_BYTES = None
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
+def base_config(b):
+    """The workload description both arms report."""
+    return {"workload": b.name + " (general LCDM+radiation+curvature batch: 4096 cosmologies x 1024 z)",
+            "B": b.B, "n_per_row": 1024, "pairs_per_gpu": int(b.nnz), "outputs": list(OUTPUTS),
+            "gradient": "fused VJP w.r.t. (H0, Om, OL, Or), random cotangents on all outputs"}
+
+
 def workload(seed_offset=0):
     from paper_2212_01937_gb300 import workloads
     b = workloads.general_batch(seed=2 + seed_offset)
@@ -116,7 +123,7 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b.nnz / v,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": b.name, "B": b.B, "n_per_row": 1024},
+            "data": "synthetic", "config": base_config(b),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
                              "sample": "%d random pairs of the workload per step (adaptive quadrature "
                                        "forward + Leibniz gradient, 1 thread)" % nsample},
@@ -248,12 +255,10 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": b.name + " (general LCDM+radiation+curvature batch: 4096 cosmologies x 1024 z)",
-                           "B": B, "n_per_row": 1024, "pairs_per_gpu": npairs, "outputs": list(OUTPUTS),
-                           "gradient": "fused VJP w.r.t. (H0, Om, OL, Or), random cotangents on all outputs",
-                           "precision": "FP32 per-pair arithmetic, FP64 root preparation and reductions",
-                           "l2": "flushed (256 MiB write) before every timed step",
-                           "launch": tune, "wall_s_timed": t_wall},
+                "config": dict(base_config(b), **{
+                    "precision": "FP32 per-pair arithmetic, FP64 root preparation and reductions",
+                    "l2": "flushed (256 MiB write) before every timed step",
+                    "launch": tune, "wall_s_timed": t_wall}),
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                         "ms_per_step": e2e_ms, "api": "lcdm_distances_vjp_host, 8 chunks, page-locked host arrays"},
