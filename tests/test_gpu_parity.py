@@ -387,3 +387,90 @@ def test_lane_maps_agree_on_sorted_redshifts(lib):
     assert torch.allclose(res["contiguous"]["grad"], res["interleaved"]["grad"], rtol=1e-12, atol=1e-12)
     t = lib.autotune(p, zt, off, outputs=("d_C", "t", "X", "mu"), cot=cot)
     assert t["lane_map"] in ("contiguous", "interleaved")
+
+
+def _cubic_three_real(a=0.5, b=0.8):
+    """(Om, OL, Or = 0) with E^2 = Om (x - a)(x - b)(x + c): three real roots,
+    two in (0, 1), so a Big Bang; c = ab / (a + b) removes the x^1 term and
+    E^2(1) = 1 fixes Om (closure)."""
+    c = a * b / (a + b)
+    Om = 1.0 / ((1 - a) * (1 - b) * (1 + c))
+    return [Om, Om * a * b * c, 0.0]
+
+
+def _quartic_four_real(a=0.5, b=0.8, c=2.0):
+    """(Om, OL, Or) with E^2 = Or (x - a)(x - b)(x + c)(x + d): four real roots,
+    d from the vanishing x^1 term, Or from E^2(1) = 1 (closure)."""
+    d = a * b * c / ((a + b) * c - a * b)
+    lam = 1.0 / ((1 - a) * (1 - b) * (1 + c) * (1 + d))
+    return [lam * ((c + d) - (a + b)), lam * a * b * c * d, lam]
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_four_real_root_quartic_vs_oracle(lib, prec):
+    """The quartic with four real roots (kind 1, both pair members real)."""
+    P = np.array([[70.0] + _quartic_four_real(), [66.0] + _quartic_four_real(0.3, 0.7, 1.5)])
+    rng = np.random.default_rng(6)
+    n = 40
+    z = rng.uniform(0.0, 20.0, P.shape[0] * n)
+    z[::n] = [1e-3, 0.05]
+    offs = np.arange(P.shape[0] + 1, dtype=np.int64) * n
+    zin = z if prec == "fp64" else z.astype(np.float32)
+    zq = zin.astype(np.float64)
+    ref, J = oracle.quad_distances(P, zq, offs, grad=True)
+    roots = lib.roots(_t(P))
+    res = lib.distances_jac(_t(P), _t(zin), _t(offs), outputs=("d_C", "t", "X", "mu"), precision=prec)
+    torch.cuda.synchronize()
+    assert roots["kind"].cpu().tolist() == [1, 1]
+    assert int(res["status"].abs().sum()) == 0
+    _check(res, ref, TOL64 if prec == "fp64" else TOL32, prec, (P, offs), names=("d_C", "t", "X"))
+    for name in ("d_C", "t", "X", "mu"):
+        got = res["jac"][name].double().cpu().numpy()
+        want = J[:, COLS[name], :]
+        err = np.abs(got - want).max(axis=1) / np.abs(want).max(axis=1)
+        assert np.all(err <= jac_tol(prec, zq, name)), (prec, name, err.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_cubic_jacobian_vs_leibniz_oracle(lib, prec):
+    """Radiationless cosmologies (Omega_r0 = 0: the cubic reduction, eqs.
+    B.1-B.3; one real root + a pair, and three real roots): Jacobians against
+    the Leibniz-rule oracle, the Omega_r0 column NaN by construction."""
+    P = np.array([[70.0, 0.3, 0.7, 0.0], [65.0, 0.5, 0.2, 0.0], [72.0] + _cubic_three_real(), [68.0, 1.4, 0.3, 0.0]])
+    rng = np.random.default_rng(4)
+    n = 30
+    z = rng.uniform(0.0, 6.0, P.shape[0] * n)
+    z[::n] = [1e-3, 0.02, 0.3, 3.0]
+    offs = np.arange(P.shape[0] + 1, dtype=np.int64) * n
+    zin = z if prec == "fp64" else z.astype(np.float32)
+    zq = zin.astype(np.float64)
+    _, J = oracle.quad_distances(P, zq, offs, grad=True)
+    res = lib.distances_jac(_t(P), _t(zin), _t(offs), outputs=("d_C", "t", "X", "mu"), precision=prec)
+    torch.cuda.synchronize()
+    assert int(res["status"].abs().sum()) == 0
+    cols = [0, 1, 2]                       # H0, Om, OL (Or has no cubic direction)
+    for name in ("d_C", "t", "X", "mu"):
+        got = res["jac"][name].double().cpu().numpy()
+        assert np.all(np.isnan(got[:, 3])), name
+        want = J[:, COLS[name], :][:, cols]
+        err = np.abs(got[:, cols] - want).max(axis=1) / np.abs(want).max(axis=1)
+        tol = jac_tol(prec, zq, name)
+        assert np.all(err <= tol), (prec, name, err.max())
+
+
+def test_autograd_function_matches_vjp(lib):
+    """lcdm.Distances (torch.autograd.Function): backward of a weighted sum of
+    the outputs equals the fused VJP entry point, and only params get a grad."""
+    b = workloads.general_batch(B=5, n=64, seed=13)
+    params = _t(b.params).requires_grad_(True)
+    z = _t(b.z.astype(np.float32))
+    off = _t(b.offsets)
+    w = {n: torch.randn(b.nnz, device=DEV, generator=torch.Generator(device=DEV).manual_seed(i))
+         for i, n in enumerate(("d_C", "mu"))}
+    d_C, mu = lib.distances_autograd(params, z, off, outputs=("d_C", "mu"), precision="fp32")
+    loss = (w["d_C"] * d_C).sum() + (w["mu"] * mu).sum()
+    loss.backward()
+    ref = lib.distances_vjp(params.detach(), z, w, off, outputs=("d_C", "mu"), precision="fp32")
+    torch.cuda.synchronize()
+    assert torch.allclose(params.grad, ref["grad"], rtol=1e-10, atol=1e-10)
+    assert z.grad is None
