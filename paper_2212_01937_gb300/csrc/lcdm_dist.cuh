@@ -121,10 +121,6 @@ template <> struct Spread<double> {
     static LCDM_HD double s0() { return 0.05; }
     enum { always_dup = 0 };
 };
-template <> struct Spread<df64> {
-    static LCDM_HD df64 s0() { return mkdf(0.1f); }
-    enum { always_dup = 0 };
-};
 
 template <int NJ, bool NEED_RD1, bool WANT_DJ, class T, int K, class PD>
 LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h, Dual<T, K>& RF,

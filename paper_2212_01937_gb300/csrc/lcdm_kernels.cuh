@@ -111,10 +111,6 @@ template <> struct IO<double> { typedef double type; };
 template <class T> LCDM_HD T recv(const double* rd, const float2* rf, int i);
 template <> LCDM_HD double recv<double>(const double* rd, const float2*, int i) { return rd[i]; }
 template <> LCDM_HD float recv<float>(const double*, const float2* rf, int i) { return rf[i].x; }
-template <> LCDM_HD df64 recv<df64>(const double*, const float2* rf, int i) {
-    float2 v = rf[i];
-    return mkdf(v.x, v.y);
-}
 
 // Build the root quantities in scalar S and evaluate the integrals.
 template <class T, int K, bool WT, bool WX> struct PairEval {
@@ -198,9 +194,6 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
     }
 };
 
-LCDM_HD float to_io(float v, float) { return v; }
-LCDM_HD double to_io(double v, double) { return v; }
-LCDM_HD float to_io(df64 v, float) { return v.hi + v.lo; }
 
 // per-pair results in the output type TO
 template <class TO, int K> struct PairOut {

@@ -28,31 +28,27 @@
 #ifndef LCDM_NI
 #define LCDM_NI __device__ __noinline__
 #endif
-// round-to-nearest float add / sub / mul that the compiler may not contract
+// round-to-nearest float add / sub that the compiler may not contract
 #ifdef __CUDA_ARCH__
 #define LCDM_FADD(a, b) __fadd_rn(a, b)
 #define LCDM_FSUB(a, b) __fsub_rn(a, b)
-#define LCDM_FMUL(a, b) __fmul_rn(a, b)
-#define LCDM_FDIV(a, b) __fdiv_rn(a, b)
 #else
 #define LCDM_FADD(a, b) ((a) + (b))
 #define LCDM_FSUB(a, b) ((a) - (b))
-#define LCDM_FMUL(a, b) ((a) * (b))
-#define LCDM_FDIV(a, b) ((a) / (b))
 #endif
 
 namespace lcdm {
 
 // ---------------------------------------------------------------------------
-// df64
+// df64: a float pair (hi + lo) used as the per-lane accumulator of the
+// per-cosmology sums in the FP32 path (no FP64 arithmetic per pair).
 // ---------------------------------------------------------------------------
 struct df64 {
     float hi, lo;
 };
 LCDM_HD df64 mkdf(float h, float l = 0.f) { df64 r; r.hi = h; r.lo = l; return r; }
 LCDM_HD df64 df_from_double(double d) { float h = (float)d; return mkdf(h, (float)(d - (double)h)); }
-LCDM_HD double df_to_double(df64 a) { return (double)a.hi + (double)a.lo; }
-// error-free sum (Knuth), sum with |a| >= |b| (Dekker), product via FMA
+// error-free sum (Knuth), sum with |a| >= |b| (Dekker)
 LCDM_HD df64 two_sum(float a, float b) {
     float s = LCDM_FADD(a, b), bb = LCDM_FSUB(s, a);
     float e = LCDM_FADD(LCDM_FSUB(a, LCDM_FSUB(s, bb)), LCDM_FSUB(b, bb));
@@ -69,57 +65,17 @@ LCDM_HD df64 operator+(df64 a, df64 b) {
     s.lo = LCDM_FADD(s.lo, t.lo);
     return fast_two_sum(s.hi, s.lo);
 }
-LCDM_HD df64 operator-(df64 a) { return mkdf(-a.hi, -a.lo); }
-LCDM_HD df64 operator-(df64 a, df64 b) { return a + (-b); }
-LCDM_HD df64 operator*(df64 a, df64 b) {
-    float p = LCDM_FMUL(a.hi, b.hi);
-    float e = fmaf(a.hi, b.hi, -p);
-    e = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-    return fast_two_sum(p, e);
-}
-LCDM_HD df64 operator/(df64 a, df64 b) {
-    float q1 = LCDM_FDIV(a.hi, b.hi);
-    df64 r = a - b * mkdf(q1);
-    float q2 = LCDM_FDIV(r.hi, b.hi);
-    r = r - b * mkdf(q2);
-    float q3 = LCDM_FDIV(r.hi, b.hi);
-    df64 q = fast_two_sum(q1, q2);
-    return q + mkdf(q3);
-}
 LCDM_HD df64 operator+(df64 a, float b) { return a + mkdf(b); }
-LCDM_HD df64 operator-(df64 a, float b) { return a - mkdf(b); }
-LCDM_HD df64 operator*(df64 a, float b) {
-    float p = LCDM_FMUL(a.hi, b);
-    float e = fmaf(a.hi, b, -p);
-    e = fmaf(a.lo, b, e);
-    return fast_two_sum(p, e);
-}
-LCDM_HD df64 operator/(df64 a, float b) { return a / mkdf(b); }
-LCDM_HD df64& operator+=(df64& a, df64 b) { a = a + b; return a; }
-LCDM_HD df64& operator-=(df64& a, df64 b) { a = a - b; return a; }
-LCDM_HD df64& operator*=(df64& a, df64 b) { a = a * b; return a; }
-// square root by one Newton-type correction of the float estimate (Karp)
-LCDM_HD df64 df_sqrt(df64 a) {
-    if (!(a.hi > 0.f)) return mkdf(a.hi == 0.f ? 0.f : nanf(""));
-    float x = 1.0f / sqrtf(a.hi);
-    float y = LCDM_FMUL(a.hi, x);
-    float p = LCDM_FMUL(y, y);
-    df64 r = a - mkdf(p, fmaf(y, y, -p));
-    return fast_two_sum(y, r.hi * (0.5f * x));
-}
 
 // ---------------------------------------------------------------------------
 // Scalar traits: value used for branching, sqrt, abs, constants.
 // ---------------------------------------------------------------------------
 LCDM_HD float sval(float a) { return a; }
 LCDM_HD double sval(double a) { return a; }
-LCDM_HD float sval(df64 a) { return a.hi; }
 LCDM_HD float ssqrt(float a) { return sqrtf(a); }
 LCDM_HD double ssqrt(double a) { return sqrt(a); }
-LCDM_HD df64 ssqrt(df64 a) { return df_sqrt(a); }
 LCDM_HD float sabs(float a) { return fabsf(a); }
 LCDM_HD double sabs(double a) { return fabs(a); }
-LCDM_HD df64 sabs(df64 a) { return a.hi < 0.f ? -a : a; }
 template <class T> struct CstImpl;
 template <> struct CstImpl<float> { static LCDM_HD float make(double v) { return (float)v; } };
 template <> struct CstImpl<double> { static LCDM_HD double make(double v) { return v; } };
@@ -128,7 +84,6 @@ template <class T> LCDM_HD T cst(double v) { return CstImpl<T>::make(v); }
 // exact multiplication by 2^e
 LCDM_HD float sldexp(float a, int e) { return ldexpf(a, e); }
 LCDM_HD double sldexp(double a, int e) { return ldexp(a, e); }
-LCDM_HD df64 sldexp(df64 a, int e) { return mkdf(ldexpf(a.hi, e), ldexpf(a.lo, e)); }
 
 // ---------------------------------------------------------------------------
 // Dual numbers (forward-mode tangents over K parameters)
@@ -225,7 +180,6 @@ template <class S> LCDM_HD typename Base<S>::type cst_like(const S&, double v) {
 // plain scalars behave as duals with no tangent
 LCDM_HD float vof(float a) { return a; }
 LCDM_HD double vof(double a) { return a; }
-LCDM_HD df64 vof(df64 a) { return a; }
 template <class T, int K> LCDM_HD T vof(const Dual<T, K>& a) { return a.v; }
 
 // ---------------------------------------------------------------------------
@@ -363,11 +317,6 @@ template <> struct Prec<float> {
 template <> struct Prec<double> {
     static LCDM_HD double tol() { return 1.5e-3; }
     static LCDM_HD double rc_series_max() { return 0.03; }
-    enum { rc_terms = 12, maxit = 40 };
-};
-template <> struct Prec<df64> {
-    static LCDM_HD df64 tol() { return mkdf(3e-3f); }
-    static LCDM_HD df64 rc_series_max() { return mkdf(0.03f); }
     enum { rc_terms = 12, maxit = 40 };
 };
 
