@@ -32,7 +32,7 @@ OUTPUTS = ("d_C", "t", "X", "mu")
 FLOP_PER_PAIR = 6529.0
 # DRAM bytes (read + write) per launch of that kernel from the same capture
 # (None once the kernel has changed since the counters were taken).
-TRAFFIC_BYTES = 131809536
+TRAFFIC_BYTES = None
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
