@@ -19,10 +19,12 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "-O3", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I" + os.path.join(ROOT, "include"), "-I" + CSRC]
 # The FP32 pair kernels divide and take square roots with the hardware's
-# approximate single-precision forms (within 2 ulp): a fraction of the
-# instructions of the IEEE-rounded sequences, well inside the FP32 error
-# budget (tested against the oracle).  FP64 arithmetic is not affected.
-FP32_PAIR_FLAGS = ["-prec-div=false", "-prec-sqrt=false"]
+# approximate single-precision forms (within 2 ulp) and flush subnormal
+# single-precision results to zero (no value or tangent of the path comes near
+# 1e-38): a fraction of the instructions of the IEEE sequences, well inside the
+# FP32 error budget (tested against the oracle).  FP64 arithmetic is not
+# affected.
+FP32_PAIR_FLAGS = ["-prec-div=false", "-prec-sqrt=false", "-ftz=true"]
 
 
 def _nvcc():
