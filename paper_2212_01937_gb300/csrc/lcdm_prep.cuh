@@ -169,7 +169,7 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
             const double rel = cnorm(w) * ddiv(1.0, cnorm(z[i]) + 1e-300);
             if (!(rel <= worst)) worst = rel;
         }
-        if (worst < 1e-30) { if (++settled >= 2) break; }
+        if (worst < 1e-30) { if (++settled >= 1) break; }
         else if (it >= 4 && worst >= 0.25 * prev) break;
         prev = worst;
     }
@@ -177,7 +177,7 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
     #pragma unroll 1
     for (int i = 0; i < n; i++) {
         #pragma unroll 1
-        for (int k = 0; k < 2; k++) {
+        for (int k = 0; k < 1; k++) {
             cd p, dp;
             horner(c, n, z[i], p, dp);
             if (dp.re == 0 && dp.im == 0) break;
