@@ -312,7 +312,7 @@ template <class T> struct Prec;
 template <> struct Prec<float> {
     static LCDM_HD float tol() { return 0.04f; }
     static LCDM_HD float rc_series_max() { return 0.1f; }
-    enum { rc_terms = 8, maxit = 24 };
+    enum { rc_terms = 6, maxit = 24 };
 };
 template <> struct Prec<double> {
     static LCDM_HD double tol() { return 1.5e-3; }
