@@ -306,11 +306,13 @@ template <class T> LCDM_HD RPair<T> pldexp(const RPair<T>& p, int e) { return mk
 // Carlson's duplication algorithm (ref. [10]).
 // Deviation tolerance: the iteration stops once every argument is within
 // tol * mean of the common mean; the truncated series is then exact to
-// about tol^6, i.e. below the working precision.
+// about c tol^6 with c < 1, at or below the working precision (FP32: 0.06,
+// which leaves the outputs as they are at 0.04 and saves a fraction of an
+// iteration per pair).
 // ---------------------------------------------------------------------------
 template <class T> struct Prec;
 template <> struct Prec<float> {
-    static LCDM_HD float tol() { return 0.04f; }
+    static LCDM_HD float tol() { return 0.06f; }
     static LCDM_HD float rc_series_max() { return 0.1f; }
     enum { rc_terms = 6, maxit = 24 };
 };
