@@ -29,10 +29,10 @@ OUTPUTS = ("d_C", "t", "X", "mu")
 # Work of the dominant kernel per pair for this workload: FP32 floating-point
 # operations (FFMA counted as 2, FADD and FMUL as 1) executed per pair, from
 # the ncu capture summarised in profiles/pairs_kernel_fp32_vjp_4096x1024.md.
-FLOP_PER_PAIR = 6529.0
+FLOP_PER_PAIR = 5501.0
 # DRAM bytes (read + write) per launch of that kernel from the same capture
 # (None once the kernel has changed since the counters were taken).
-TRAFFIC_BYTES = None
+TRAFFIC_BYTES = 131349248
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 
 
