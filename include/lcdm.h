@@ -29,8 +29,11 @@
  *            npairs = n (CSR) or B*n (DENSE, SHARED).
  *   dtype    precision LCDM_FP64: z, outputs, cotangents, Jacobians and
  *            m_obs are float64 and every step is FP64.  LCDM_FP32_MIXED: they
- *            are float32 and the per-pair arithmetic is FP32; the root solve
- *            and all per-cosmology reductions stay FP64.
+ *            are float32 and the per-pair arithmetic is FP32 (division and
+ *            square root within 2 ulp, subnormal results flushed to zero);
+ *            the root solve and all per-cosmology reductions stay FP64.
+ *   domain   z >= 0 (the integrals run from 0 to z); outputs for negative z
+ *            are unspecified.
  *   units    d_C, d_M, d_L, X in Mpc; t in Gyr; mu in magnitudes.
  *   memory   every pointer argument except opts is a DEVICE pointer owned by
  *            the caller; the library allocates nothing.  Scratch comes from
