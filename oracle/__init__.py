@@ -5,9 +5,11 @@ TEST INFRASTRUCTURE ONLY: only ``tests/``, ``__graft_entry__.smoke()`` and the
 It shares no code with the CUDA path and never calls it.
 
 * O1: adaptive quadrature of the defining integrals (2.3)-(2.5) in the scale
-  factor, with the curvature map and distance modulus (Sec. 2.1.1, fn22).
+  factor, with the curvature map and distance modulus (Sec. 2.1.1, fn22), for
+  z1 = 0, general limits z1 <= z2, and z2 -> infinity (age, horizon).
 * O4: Leibniz-rule gradients of the same integrals (the approach fn23 names).
-* O2: eqs. (3.7)-(3.9) / (B.1)-(B.3) assembled in complex FP64 from roots.
+* O2: eqs. (3.7)-(3.9) / (B.1)-(B.3) assembled in complex FP64 from roots,
+  for any limits z1 <= z2 (Sec. 3.1), and their z2 -> infinity limits.
 * O3: roots of E^2 by companion-matrix eigenvalues (Sec. 3, fn12) with Newton
   polishing, and their derivatives by App. A, eqs. (A.1)-(A.4).
 
@@ -15,11 +17,13 @@ Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 (closed forms, identities, library cross-checks, brute force).
 """
 from .core import (carlson, quad_distances, carlson_distances, simpson,
-                   set_mutation, OUT_NAMES)
+                   set_mutation, OUT_NAMES, quad_between, quad_limits,
+                   carlson_between, carlson_limits)
 from .roots import (poly_coeffs_x, roots_x, root_coef_jacobian,
                     root_param_jacobian, classify_roots, permutations)
 
 __all__ = ["carlson", "quad_distances", "carlson_distances", "simpson",
+           "quad_between", "quad_limits", "carlson_between", "carlson_limits",
            "set_mutation", "OUT_NAMES", "poly_coeffs_x", "roots_x",
            "root_coef_jacobian", "root_param_jacobian", "classify_roots",
            "permutations"]

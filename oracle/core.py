@@ -21,6 +21,12 @@ def _load():
                                               ctypes.c_int64, ctypes.c_double, dp, dp]
         lib.oracle_carlson_distances.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp,
                                                  ctypes.c_int64, dp, i32p, i32p, dp, dp]
+        lib.oracle_quad_between.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp, dp,
+                                            ctypes.c_int64, ctypes.c_double, dp, dp]
+        lib.oracle_quad_limits.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, ctypes.c_double, dp, dp]
+        lib.oracle_carlson_between.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp, dp,
+                                               ctypes.c_int64, dp, i32p, i32p, dp, dp]
+        lib.oracle_carlson_limits.argtypes = [dp, ctypes.c_int64, ctypes.c_int, dp, dp, i32p, i32p, dp, dp]
         lib.oracle_carlson_batch.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp]
         lib.oracle_simpson.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp]
         lib.oracle_set_mutation.argtypes = [ctypes.c_int]
@@ -110,6 +116,88 @@ def carlson_distances(params, z, offsets=None, roots=None, perm=None, return_ima
         _dp(params), B, ncol, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
         _dp(z), z.size, _dp(packed), nroot.ctypes.data_as(i32p), perm.ctypes.data_as(i32p),
         _dp(out), _dp(imag))
+    return (out, imag) if return_imag else out
+
+
+def _z1(z1, B):
+    z1 = np.ascontiguousarray(np.broadcast_to(np.asarray(z1, dtype=np.float64), (B,)))
+    return z1
+
+
+def quad_between(params, z1, z2, offsets=None, rtol=1e-14, grad=False):
+    """O1 (+ O4) with general limits: eqs. (2.3)-(2.5) from z1[b] (per row) to
+    z2[j] (per pair).  Outputs as quad_distances; d_M is the transverse
+    comoving distance S_k(chi(z1, z2)) and d_L = (1+z2) d_M / (1+z1)^2 (a
+    source at z2 seen by a comoving observer at z1).  z2 < z1 gives NaN."""
+    params, z2, offsets, B, ncol = _csr(params, z2, offsets)
+    z1 = _z1(z1, B)
+    out = np.zeros((z2.size, 6))
+    jac = np.zeros((z2.size, 6, ncol)) if grad else None
+    _load().oracle_quad_between(
+        _dp(params), B, ncol, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        _dp(z1), _dp(z2), z2.size, rtol, _dp(out), _dp(jac) if grad else None)
+    return (out, jac) if grad else out
+
+
+def quad_limits(params, z1, rtol=1e-14, grad=False):
+    """O1 (+ O4) with the upper limit at infinity, per row: out[B, 2] =
+    (chi(z1, inf) [Mpc], t(z1, inf) [Gyr]) -- the comoving distance to the
+    particle horizon and the age of the universe at z1 (Sec. 2.1.1)."""
+    params = np.ascontiguousarray(np.atleast_2d(params), dtype=np.float64)
+    B, ncol = params.shape
+    z1 = _z1(z1, B)
+    out = np.zeros((B, 2))
+    jac = np.zeros((B, 2, ncol)) if grad else None
+    _load().oracle_quad_limits(_dp(params), B, ncol, _dp(z1), rtol, _dp(out),
+                               _dp(jac) if grad else None)
+    return (out, jac) if grad else out
+
+
+def _roots_perm(params, roots, perm):
+    from . import roots as _roots
+    if roots is None:
+        rho, nroot = _roots.roots_x(params)
+    else:
+        rho, nroot = roots
+    if perm is None:
+        perm = _roots.permutations(rho, nroot)
+    B = params.shape[0]
+    packed = np.zeros((B, 4, 2))
+    packed[:, :, 0] = rho.real
+    packed[:, :, 1] = rho.imag
+    return (np.ascontiguousarray(packed), np.ascontiguousarray(nroot, dtype=np.int32),
+            np.ascontiguousarray(perm, dtype=np.int32))
+
+
+def carlson_between(params, z1, z2, offsets=None, roots=None, perm=None, return_imag=False):
+    """O2 with general limits: eqs. (3.7)-(3.9) / (B.1)-(B.3) with
+    X_m = sqrt(z2 - r_m), Y_m = sqrt(z1 - r_m) (Sec. 3.1); outputs as
+    quad_between."""
+    params, z2, offsets, B, ncol = _csr(params, z2, offsets)
+    z1 = _z1(z1, B)
+    packed, nroot, perm = _roots_perm(params, roots, perm)
+    out = np.zeros((z2.size, 6))
+    imag = np.zeros((z2.size, 3))
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _load().oracle_carlson_between(
+        _dp(params), B, ncol, offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        _dp(z1), _dp(z2), z2.size, _dp(packed), nroot.ctypes.data_as(i32p), perm.ctypes.data_as(i32p),
+        _dp(out), _dp(imag))
+    return (out, imag) if return_imag else out
+
+
+def carlson_limits(params, z1, roots=None, perm=None, return_imag=False):
+    """O2 limits z2 -> infinity of eqs. (3.7)/(3.8) and (B.1)/(B.2), per row:
+    out[B, 2] = (chi(z1, inf) [Mpc], t(z1, inf) [Gyr])."""
+    params = np.ascontiguousarray(np.atleast_2d(params), dtype=np.float64)
+    B, ncol = params.shape
+    z1 = _z1(z1, B)
+    packed, nroot, perm = _roots_perm(params, roots, perm)
+    out = np.zeros((B, 2))
+    imag = np.zeros((B, 2))
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _load().oracle_carlson_limits(_dp(params), B, ncol, _dp(z1), _dp(packed), nroot.ctypes.data_as(i32p),
+                                  perm.ctypes.data_as(i32p), _dp(out), _dp(imag))
     return (out, imag) if return_imag else out
 
 

@@ -42,6 +42,8 @@ typedef double complex cplx;
 /*   4: drop the (1+z) factor of the luminosity distance                     */
 /*   5: drop the -a^2 closure term from the Omega_m Leibniz gradient          */
 /*   6: replace R_C(1, 1+e_m) by 1 in the duplication sum of R_J            */
+/*   7: use sqrt(-r) for Y_m = sqrt(z1 - r_m) (forget the lower limit)      */
+/*   8: drop the R_C term of the z2 -> infinity limit of eq. (3.8)          */
 /* ------------------------------------------------------------------------ */
 static int g_mutation = 0;
 void oracle_set_mutation(int m) { g_mutation = m; }
@@ -285,18 +287,25 @@ static void integrand(double a, const cosmo_t* c, double* out) {
     }
 }
 
-/* 15-point rule on [lo, hi] of the variable t; the scale factor is a = t
- * (mode 0) or a = 1 - t (mode 1, used next to a = 1 so that the width of a
- * short interval z/(1+z) is exact). */
-static void gl_rule(const cosmo_t* c, int mode, double lo, double hi, double* res, double* absres) {
+/* 15-point rule on [lo, hi] of the variable t.  The scale factor is
+ *   mode 0: a = t;
+ *   mode 1: a = anchor - t, next to the upper end a = anchor of the range, so
+ *           that the width of a short interval, (z2 - z1)/((1+z1)(1+z2)), is
+ *           exact;
+ *   mode 2: a = t^2 with da = 2t dt, down to a = 0 (the z2 -> infinity limit,
+ *           where the radiationless integrands grow like a^-1/2). */
+static void gl_rule(const cosmo_t* c, int mode, double anchor, double lo, double hi, double* res,
+                    double* absres) {
     double h = 0.5 * (hi - lo), mid = 0.5 * (hi + lo), v[NCOMP];
     for (int k = 0; k < NCOMP; k++) { res[k] = 0; if (absres) absres[k] = 0; }
     for (int i = 0; i < NGL; i++) {
         double tt = mid + h * gl_x[i];
-        integrand(mode ? 1.0 - tt : tt, c, v);
+        double a = mode == 0 ? tt : (mode == 1 ? anchor - tt : tt * tt);
+        double wt = mode == 2 ? 2.0 * tt : 1.0;
+        integrand(a, c, v);
         for (int k = 0; k < NCOMP; k++) {
-            res[k] += gl_w[i] * h * v[k];
-            if (absres) absres[k] += gl_w[i] * h * fabs(v[k]);
+            res[k] += gl_w[i] * h * wt * v[k];
+            if (absres) absres[k] += gl_w[i] * h * wt * fabs(v[k]);
         }
     }
 }
@@ -307,9 +316,14 @@ static void gl_rule(const cosmo_t* c, int mode, double lo, double hi, double* re
  * about rtol).  At most MAX_INTERVALS intervals are evaluated; the return
  * value is the number of accepted intervals, negative if the cap was hit. */
 #define MAX_INTERVALS 200000
-static int adapt(const cosmo_t* c, int mode, double lo, double hi, double rtol, double* total) {
+#define KMASK_ALL 0x7fff
+/* every component except the absorption distance and its derivatives (which
+ * diverge as z2 -> infinity) */
+#define KMASK_NO_X (KMASK_ALL & ~((1 << 2) | (0xf << 11)))
+static int adapt(const cosmo_t* c, int mode, double anchor, double lo, double hi, double rtol, int kmask,
+                 double* total) {
     double whole[NCOMP], wabs[NCOMP];
-    gl_rule(c, mode, lo, hi, whole, wabs);
+    gl_rule(c, mode, anchor, lo, hi, whole, wabs);
     for (int k = 0; k < NCOMP; k++) total[k] = 0;
     static double stk_lo[256], stk_hi[256], stk_v[256][NCOMP];
     int sp = 0, nacc = 0, nev = 0, capped = 0;
@@ -321,11 +335,12 @@ static int adapt(const cosmo_t* c, int mode, double lo, double hi, double rtol, 
         double a = stk_lo[sp], b = stk_hi[sp], m = 0.5 * (a + b);
         double I1[NCOMP], L[NCOMP], R[NCOMP], La[NCOMP], Ra[NCOMP];
         memcpy(I1, stk_v[sp], sizeof(I1));
-        gl_rule(c, mode, a, m, L, La);
-        gl_rule(c, mode, m, b, R, Ra);
+        gl_rule(c, mode, anchor, a, m, L, La);
+        gl_rule(c, mode, anchor, m, b, R, Ra);
         nev++;
         int ok = 1;
         for (int k = 0; k < NCOMP; k++) {
+            if (!(kmask >> k & 1)) continue;
             double err = fabs(L[k] + R[k] - I1[k]);
             if (err > rtol * (La[k] + Ra[k]) && err > 1e-300) { ok = 0; break; }
         }
@@ -377,23 +392,48 @@ static int quad_breakpoints(const cosmo_t* c, double lo, double hi, double* bp) 
     return m;
 }
 
-/* Adaptive quadrature over [lo, hi] of t (mode as in gl_rule), split at the
- * breakpoints (mapped to t when mode == 1); results added to total. */
-static void integrate_pieces(const cosmo_t* c, int mode, double lo, double hi, double rtol, double* total) {
+/* Adaptive quadrature over [lo, hi] of t (mode and anchor as in gl_rule),
+ * split at the breakpoints (mapped to t); results added to total. */
+static void integrate_pieces(const cosmo_t* c, int mode, double anchor, double lo, double hi, double rtol,
+                             int kmask, double* total) {
     double bp[64], part[NCOMP];
-    double alo = mode ? 1.0 - hi : lo, ahi = mode ? 1.0 - lo : hi;
+    double alo = mode == 0 ? lo : (mode == 1 ? anchor - hi : lo * lo);
+    double ahi = mode == 0 ? hi : (mode == 1 ? anchor - lo : hi * hi);
     int m = quad_breakpoints(c, alo, ahi, bp);
     double t[66];
     int nt = 0;
     t[nt++] = lo;
     for (int i = 0; i < m; i++) {
-        double v = mode ? 1.0 - bp[m - 1 - i] : bp[i];
+        double v = mode == 0 ? bp[i] : (mode == 1 ? anchor - bp[m - 1 - i] : sqrt(bp[i]));
         if (v > t[nt - 1] && v < hi) t[nt++] = v;
     }
     t[nt++] = hi;
     for (int i = 0; i + 1 < nt; i++) {
-        adapt(c, mode, t[i], t[i + 1], rtol, part);
+        adapt(c, mode, anchor, t[i], t[i + 1], rtol, kmask, part);
         for (int k = 0; k < NCOMP; k++) total[k] += part[k];
+    }
+}
+
+/* The NCOMP integrals over z in [z1, z2] (z2 may be +infinity), i.e. over
+ * a in [a2, a1] with a = 1/(1+z).  Next to a1 the variable is s = a1 - a over
+ * [0, min(w, a1/2)], w = a1 - a2 = (z2 - z1)/((1+z1)(1+z2)) formed without
+ * cancellation; the rest, [a2, a1/2], is integrated in a itself (in sqrt(a)
+ * when a2 = 0).  Each part is further split at the breakpoints of
+ * quad_breakpoints. */
+static void integrate_between(const cosmo_t* c, double z1, double z2, double rtol, int kmask, double* Iv) {
+    const int inf = isinf(z2);
+    const double a1 = 1.0 / (1.0 + z1);
+    const double w = inf ? a1 : (z2 - z1) / ((1.0 + z1) * (1.0 + z2));
+    double I2[NCOMP];
+    for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
+    integrate_pieces(c, 1, a1, 0.0, w < 0.5 * a1 ? w : 0.5 * a1, rtol, kmask, Iv);
+    if (w > 0.5 * a1) {
+        for (int k = 0; k < NCOMP; k++) I2[k] = 0.0;
+        if (inf)
+            integrate_pieces(c, 2, 0.0, 0.0, sqrt(0.5 * a1), rtol, kmask, I2);
+        else
+            integrate_pieces(c, 0, 0.0, 1.0 / (1.0 + z2), 0.5 * a1, rtol, kmask, I2);
+        for (int k = 0; k < NCOMP; k++) Iv[k] += I2[k];
     }
 }
 
@@ -414,7 +454,64 @@ static int64_t row_of(const int64_t* offsets, int64_t B, int64_t nnz, int64_t j)
     return lo;
 }
 
-/* O1 (+ O4 when jac != NULL).
+/* O1 (+ O4) for one pair of limits z1 <= z2 (z2 finite), cosmology c:
+ * o[6] = (chi, t, d_abs, d_M, d_L, mu) of eqs. (2.3)-(2.5) and Sec. 2.1.1;
+ * J[6][ncol] (may be NULL) their derivatives w.r.t. the parameter columns.
+ * d_M is the transverse comoving distance S_k(chi) between the two
+ * redshifts; d_L = (1+z2) d_M / (1+z1)^2 is the luminosity distance of a
+ * source at z2 seen by a comoving observer at z1 (the source's redshift
+ * relative to that observer is (1+z2)/(1+z1) - 1; with z1 = 0 this is the
+ * usual (1+z) d_M). */
+static void quad_pair(const cosmo_t* c, double H0, int ncol, double z1, double z2, double rtol, double* o,
+                      double* J) {
+    double DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0;
+    double Iv[NCOMP];
+    if (z2 == z1) {
+        for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
+    } else {
+        integrate_between(c, z1, z2, rtol, KMASK_ALL, Iv);
+    }
+    double S, SD, Sk;
+    curv_map(Iv[0], c->Ok, &S, &SD, &Sk);
+    double lf = (g_mutation == 4 ? 1.0 : 1.0 + z2) / ((1.0 + z1) * (1.0 + z1));
+    double dC = DH * Iv[0], t = tH * Iv[1], X = DH * Iv[2], dM = DH * S;
+    double dL = lf * dM;
+    double mu = 5.0 * log10(dL) + 25.0;
+    o[0] = dC; o[1] = t; o[2] = X; o[3] = dM; o[4] = dL; o[5] = mu;
+    if (!J) return;
+    /* H0: every distance and time scales as 1/H0. */
+    for (int k = 0; k < 5; k++) J[k * ncol + 0] = -o[k] / H0;
+    J[5 * ncol + 0] = -5.0 / (log(10.0) * H0);
+    /* Omega directions: dI_w/dtheta = sum_g (dQ/dtheta)_g-coefficients x J_w[g]. */
+    for (int ip = 1; ip < ncol; ip++) {
+        /* coefficients of (a, a^4, 1, a^2) in dQ/dtheta, and dOk/dtheta */
+        double cg[4] = {0, 0, 0, 0}, dOk = 0;
+        if (ip == 1) cg[0] = 1;
+        if (ip == 2) cg[1] = 1;
+        if (ip == 3) cg[2] = 1;
+        if (ip == 4) cg[3] = 1;
+        if (ncol == 4) { /* closure: Ok = 1 - Om - OL - Or */
+            if (!(g_mutation == 5 && ip == 1)) cg[3] = -1;
+            dOk = -1;
+        } else if (ip == 4) {
+            dOk = 1;
+        }
+        double dI[3];
+        for (int iw = 0; iw < 3; iw++) {
+            dI[iw] = 0;
+            for (int ig = 0; ig < 4; ig++) dI[iw] += cg[ig] * Iv[3 + 4 * iw + ig];
+        }
+        double ddM = DH * (SD * dI[0] + Sk * dOk);
+        J[0 * ncol + ip] = DH * dI[0];
+        J[1 * ncol + ip] = tH * dI[1];
+        J[2 * ncol + ip] = DH * dI[2];
+        J[3 * ncol + ip] = ddM;
+        J[4 * ncol + ip] = lf * ddM;
+        J[5 * ncol + ip] = (z2 == z1) ? 0.0 : 5.0 / log(10.0) * ddM / dM;
+    }
+}
+
+/* O1 (+ O4 when jac != NULL), z1 = 0 and z2 = z for every pair.
  * params [B][ncol] = (H0, Om, OL, Or[, Ok]); z [nnz]; rows by offsets.
  * out [nnz][6] = (d_C, t, X, d_M, d_L, mu) in Mpc / Gyr / mag.
  * jac [nnz][6][ncol]: d out / d params (H0 first).
@@ -427,80 +524,84 @@ int oracle_quad_distances(const double* params, int64_t B, int ncol, const int64
         double H0;
         cosmo_t c;
         unpack_params(params + b * ncol, ncol, &H0, &c);
-        double zz = z[j], DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0;
-        double Iv[NCOMP];
-        if (zz == 0.0) {
-            for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
-        } else {
-            /* [a(z), 1] split at a = 1/2: near a = 1 integrate in s = 1 - a over
-             * [0, min(z/(1+z), 1/2)]; below a = 1/2 integrate in a itself.  Each
-             * part is further split at the breakpoints of quad_breakpoints. */
-            double w = zz / (1.0 + zz), I2[NCOMP];
-            for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
-            integrate_pieces(&c, 1, 0.0, w < 0.5 ? w : 0.5, rtol, Iv);
-            if (w > 0.5) {
-                for (int k = 0; k < NCOMP; k++) I2[k] = 0.0;
-                integrate_pieces(&c, 0, 1.0 / (1.0 + zz), 0.5, rtol, I2);
-                for (int k = 0; k < NCOMP; k++) Iv[k] += I2[k];
-            }
+        quad_pair(&c, H0, ncol, 0.0, z[j], rtol, out + 6 * j, jac ? jac + 6 * ncol * j : NULL);
+    }
+    return 0;
+}
+
+/* O1 (+ O4) with general limits (eqs. 2.3-2.5 as defined, z1 <= z2): the
+ * lower limit z1[b] per row, the upper limit z2[j] per pair; outputs as in
+ * quad_pair.  Pairs with z2 < z1 give NaN. */
+int oracle_quad_between(const double* params, int64_t B, int ncol, const int64_t* offsets, const double* z1,
+                        const double* z2, int64_t nnz, double rtol, double* out, double* jac) {
+    if (!gl_ready) gl_init();
+    for (int64_t j = 0; j < nnz; j++) {
+        int64_t b = row_of(offsets, B, nnz, j);
+        double H0;
+        cosmo_t c;
+        unpack_params(params + b * ncol, ncol, &H0, &c);
+        if (!(z2[j] >= z1[b])) {
+            for (int k = 0; k < 6; k++) out[6 * j + k] = NAN;
+            if (jac) for (int k = 0; k < 6 * ncol; k++) jac[6 * ncol * j + k] = NAN;
+            continue;
         }
-        double S, SD, Sk;
-        curv_map(Iv[0], c.Ok, &S, &SD, &Sk);
-        double dC = DH * Iv[0], t = tH * Iv[1], X = DH * Iv[2], dM = DH * S;
-        double dL = (g_mutation == 4 ? 1.0 : 1.0 + zz) * dM;
-        double mu = 5.0 * log10(dL) + 25.0;
-        double* o = out + 6 * j;
-        o[0] = dC; o[1] = t; o[2] = X; o[3] = dM; o[4] = dL; o[5] = mu;
+        quad_pair(&c, H0, ncol, z1[b], z2[j], rtol, out + 6 * j, jac ? jac + 6 * ncol * j : NULL);
+    }
+    return 0;
+}
+
+/* O1 (+ O4) for the upper limit z2 -> infinity, per row b with lower limit
+ * z1[b] (Sec. 2.1.1: the age of the universe at z1 is t(z1, infinity)):
+ * out [B][2] = (chi(z1, inf) [Mpc], the comoving distance to the particle
+ * horizon; t(z1, inf) [Gyr], the age), jac [B][2][ncol]. */
+int oracle_quad_limits(const double* params, int64_t B, int ncol, const double* z1, double rtol, double* out,
+                       double* jac) {
+    if (!gl_ready) gl_init();
+    for (int64_t b = 0; b < B; b++) {
+        double H0;
+        cosmo_t c;
+        unpack_params(params + b * ncol, ncol, &H0, &c);
+        double DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0, Iv[NCOMP];
+        integrate_between(&c, z1[b], INFINITY, rtol, KMASK_NO_X, Iv);
+        out[2 * b] = DH * Iv[0];
+        out[2 * b + 1] = tH * Iv[1];
         if (!jac) continue;
-        double* J = jac + 6 * ncol * j;
-        /* H0: every distance and time scales as 1/H0. */
-        for (int k = 0; k < 5; k++) J[k * ncol + 0] = -o[k] / H0;
-        J[5 * ncol + 0] = -5.0 / (log(10.0) * H0);
-        /* Omega directions: dI_w/dtheta = sum_g (dQ/dtheta)_g-coefficients x J_w[g]. */
+        double* J = jac + 2 * ncol * b;
+        J[0] = -out[2 * b] / H0;
+        J[ncol] = -out[2 * b + 1] / H0;
         for (int ip = 1; ip < ncol; ip++) {
-            /* coefficients of (a, a^4, 1, a^2) in dQ/dtheta, and dOk/dtheta */
-            double cg[4] = {0, 0, 0, 0}, dOk = 0;
-            if (ip == 1) cg[0] = 1;
-            if (ip == 2) cg[1] = 1;
-            if (ip == 3) cg[2] = 1;
-            if (ip == 4) cg[3] = 1;
-            if (ncol == 4) { /* closure: Ok = 1 - Om - OL - Or */
-                if (!(g_mutation == 5 && ip == 1)) cg[3] = -1;
-                dOk = -1;
-            } else if (ip == 4) {
-                dOk = 1;
-            }
-            double dI[3];
-            for (int iw = 0; iw < 3; iw++) {
-                dI[iw] = 0;
-                for (int ig = 0; ig < 4; ig++) dI[iw] += cg[ig] * Iv[3 + 4 * iw + ig];
-            }
-            double ddM = DH * (SD * dI[0] + Sk * dOk);
-            J[0 * ncol + ip] = DH * dI[0];
-            J[1 * ncol + ip] = tH * dI[1];
-            J[2 * ncol + ip] = DH * dI[2];
-            J[3 * ncol + ip] = ddM;
-            J[4 * ncol + ip] = (1.0 + zz) * ddM;
-            J[5 * ncol + ip] = (zz == 0.0) ? 0.0 : 5.0 / log(10.0) * ddM / dM;
+            double cg[4] = {0, 0, 0, 0};
+            cg[ip - 1] = 1;
+            if (ncol == 4) cg[3] = -1;
+            double d0 = 0, d1 = 0;
+            for (int ig = 0; ig < 4; ig++) { d0 += cg[ig] * Iv[3 + ig]; d1 += cg[ig] * Iv[7 + ig]; }
+            J[ip] = DH * d0;
+            J[ncol + ip] = tH * d1;
         }
     }
     return 0;
 }
 
 /* ======================================================================== */
-/* O2: Carlson formulas (3.7)-(3.9) and (B.1)-(B.3), z1 = 0, z2 = z.        */
+/* O2: Carlson formulas (3.7)-(3.9) and (B.1)-(B.3) for limits z1 <= z2,    */
+/* with X_m = sqrt(z2 - r_m), Y_m = sqrt(z1 - r_m) and Delta z = z2 - z1     */
+/* as defined in Sec. 3.1; and their limits as z2 -> infinity.              */
 /* ======================================================================== */
+
+/* Y_m = sqrt(z1 - r_m) (mutation 7 drops z1 here) */
+static cplx lower_root(double z1, cplx r) { return csqrt((g_mutation == 7 ? 0.0 : z1) - r); }
 
 /* Quartic, eqs. (3.7)-(3.9).  r[4]: roots of E^2 in z.  it: index i for t;
  * (iX, lX): indices i and l for X; the remaining two are j, k.  Outputs
  * chi, t, X in units of c/H0, 1/H0, c/H0 with the Or^-1/2 prefactor
  * included; im[3] receives the imaginary parts (should vanish). */
-static void quartic_carlson(const cplx* r, double Or, double z, int it, int iX, int lX,
+static void quartic_carlson(const cplx* r, double Or, double z1, double z2, int it, int iX, int lX,
                             double* res, double* im) {
     cplx X[4], Y[4];
+    const double dz = z2 - z1;
     for (int m = 0; m < 4; m++) {
-        X[m] = csqrt(z - r[m]);
-        Y[m] = csqrt(-r[m]);
+        X[m] = csqrt(z2 - r[m]);
+        Y[m] = lower_root(z1, r[m]);
         if (g_mutation == 3) { cplx s = X[m]; X[m] = Y[m]; Y[m] = s; }
     }
     /* u_ab = X_a X_b Y_c Y_d + Y_a Y_b X_c X_d, {c,d} the complement of {a,b} */
@@ -513,7 +614,7 @@ static void quartic_carlson(const cplx* r, double Or, double z, int it, int iX, 
     cplx u12, u13, u14;
     UAB(0, 1, u12); UAB(0, 2, u13); UAB(0, 3, u14);
     cplx rf = oracle_rf(u12 * u12, u13 * u13, u14 * u14);
-    cplx chi = Or_h * 2.0 * z * rf;
+    cplx chi = Or_h * 2.0 * dz * rf;
     /* ---- t, eq. (3.8), with the index i = it ---- */
     {
         int i = it, o[3], n = 0;
@@ -524,16 +625,16 @@ static void quartic_carlson(const cplx* r, double Or, double z, int it, int iX, 
         Ut[0] = uij * uij; Ut[1] = uik * uik; Ut[2] = uil * uil;
         cplx dij = r[j] - r[i], dik = r[k] - r[i], dil = r[l] - r[i];
         cplx di5 = -(1.0 + r[i]), dj5 = -(1.0 + r[j]), dk5 = -(1.0 + r[k]), dl5 = -(1.0 + r[l]);
-        cplx ui5 = Ut[0] - z * z * dik * dil * dj5 / di5;
-        cplx qi5 = (1.0 + z) / ((-r[i]) * (z - r[i])) * ui5;
-        cplx si5 = qi5 + z * z * dk5 * dl5 * dj5 / di5;
+        cplx ui5 = Ut[0] - dz * dz * dik * dil * dj5 / di5;
+        cplx qi5 = (z1 + 1.0) * (z2 + 1.0) / ((z1 - r[i]) * (z2 - r[i])) * ui5;
+        cplx si5 = qi5 + dz * dz * dk5 * dl5 * dj5 / di5;
         if (fabs(cimag(ui5)) <= 1e-13 * cabs(ui5)) ui5 = creal(ui5);
         if (fabs(cimag(qi5)) <= 1e-13 * cabs(qi5)) qi5 = creal(qi5);
         if (fabs(cimag(si5)) <= 1e-13 * cabs(si5)) si5 = creal(si5);
         cplx rfi = oracle_rf(Ut[0], Ut[1], Ut[2]);
-        cplx br = z * z / 3.0 * dij * dik * dil / di5 * oracle_rj(Ut[0], Ut[1], Ut[2], ui5)
+        cplx br = dz * dz / 3.0 * dij * dik * dil / di5 * oracle_rj(Ut[0], Ut[1], Ut[2], ui5)
                   + (g_mutation == 2 ? -1.0 : 1.0) * oracle_rc(si5, qi5);
-        cplx t = Or_h * 2.0 * z / (r[i] + 1.0) * (rfi - br);
+        cplx t = Or_h * 2.0 * dz / (r[i] + 1.0) * (rfi - br);
         res[1] = creal(t); im[1] = cimag(t);
     }
     /* ---- X, eq. (3.9), with indices i = iX, l = lX ---- */
@@ -546,21 +647,21 @@ static void quartic_carlson(const cplx* r, double Or, double z, int it, int iX, 
         cplx U0 = uij * uij, U1 = uik * uik, U2 = uil * uil;
         cplx dij = r[j] - r[i], dik = r[k] - r[i], dil = r[l] - r[i];
         cplx djl = r[l] - r[j], dkl = r[l] - r[k];
-        cplx ui0 = U0 - z * z * dik * dil;
-        cplx qi0 = ui0 / ((-r[i]) * (z - r[i]));
-        cplx si0 = qi0 + z * z;
+        cplx ui0 = U0 - dz * dz * dik * dil;
+        cplx qi0 = ui0 / ((z1 - r[i]) * (z2 - r[i]));
+        cplx si0 = qi0 + dz * dz;
         if (fabs(cimag(ui0)) <= 1e-13 * cabs(ui0)) ui0 = creal(ui0);
         if (fabs(cimag(qi0)) <= 1e-13 * cabs(qi0)) qi0 = creal(qi0);
         if (fabs(cimag(si0)) <= 1e-13 * cabs(si0)) si0 = creal(si0);
         cplx sumr = r[0] + r[1] + r[2] + r[3] + 4.0;
         cplx rfx = oracle_rf(U0, U1, U2);
-        cplx term0 = (X[i] * X[j] * X[k] / X[l] - Y[i] * Y[j] * Y[k] / Y[l]) / z;
+        cplx term0 = (X[i] * X[j] * X[k] / X[l] - Y[i] * Y[j] * Y[k] / Y[l]) / dz;
         cplx term1 = (2.0 * (r[i] + 1.0) * (r[i] + 1.0) - dij * dik) * rfx;
-        cplx term2 = djl * dkl * (z * z / 3.0 * dij * dik * oracle_rd(U0, U1, U2)
+        cplx term2 = djl * dkl * (dz * dz / 3.0 * dij * dik * oracle_rd(U0, U1, U2)
                                   + X[i] * Y[i] / (X[l] * Y[l]) / uil);
-        cplx term3 = sumr * (z * z / 3.0 * dij * dik * dil / (-1.0) * oracle_rj(U0, U1, U2, ui0)
+        cplx term3 = sumr * (dz * dz / 3.0 * dij * dik * dil / (-1.0) * oracle_rj(U0, U1, U2, ui0)
                              + oracle_rc(si0, qi0));
-        cplx Xd = Or_h * z * (term0 + term1 + term2 + term3);
+        cplx Xd = Or_h * dz * (term0 + term1 + term2 + term3);
         res[2] = creal(Xd); im[2] = cimag(Xd);
     }
     res[0] = creal(chi); im[0] = cimag(chi);
@@ -568,11 +669,12 @@ static void quartic_carlson(const cplx* r, double Or, double z, int it, int iX, 
 }
 
 /* Cubic (Or = 0), eqs. (B.1)-(B.3); r[3] roots of E^2 in z, i = index i. */
-static void cubic_carlson(const cplx* r, double Om, double z, int i, double* res, double* im) {
+static void cubic_carlson(const cplx* r, double Om, double z1, double z2, int i, double* res, double* im) {
     cplx X[3], Y[3];
+    const double dz = z2 - z1;
     for (int m = 0; m < 3; m++) {
-        X[m] = csqrt(z - r[m]);
-        Y[m] = csqrt(-r[m]);
+        X[m] = csqrt(z2 - r[m]);
+        Y[m] = lower_root(z1, r[m]);
         if (g_mutation == 3) { cplx s = X[m]; X[m] = Y[m]; Y[m] = s; }
     }
     cplx u[3];
@@ -584,60 +686,159 @@ static void cubic_carlson(const cplx* r, double Om, double z, int i, double* res
     cplx U[3] = {u[0] * u[0], u[1] * u[1], u[2] * u[2]};
     double Om_h = 1.0 / sqrt(Om);
     cplx rf = oracle_rf(U[0], U[1], U[2]);
-    cplx chi = Om_h * 2.0 * z * rf;
-    cplx ui5 = U[i] + z * z * (r[i] + 1.0);
-    cplx s5 = Y[0] * Y[1] * Y[2] * (z + 1.0) + X[0] * X[1] * X[2];
-    cplx qi5 = (1.0 + z) * ui5;
+    cplx chi = Om_h * 2.0 * dz * rf;
+    cplx ui5 = U[i] + dz * dz * (r[i] + 1.0);
+    cplx s5 = Y[0] * Y[1] * Y[2] * (z2 + 1.0) + X[0] * X[1] * X[2] * (z1 + 1.0);
+    cplx qi5 = (z1 + 1.0) * (z2 + 1.0) * ui5;
     if (fabs(cimag(ui5)) <= 1e-13 * cabs(ui5)) ui5 = creal(ui5);
     if (fabs(cimag(qi5)) <= 1e-13 * cabs(qi5)) qi5 = creal(qi5);
     cplx s52 = s5 * s5;
     if (fabs(cimag(s52)) <= 1e-13 * cabs(s52)) s52 = creal(s52);
-    cplx t = Om_h * 2.0 * z * (z * z / 3.0 * oracle_rj(U[0], U[1], U[2], ui5)
-                               + (g_mutation == 2 ? -1.0 : 1.0) * oracle_rc(s52, qi5));
+    cplx t = Om_h * 2.0 * dz * (dz * dz / 3.0 * oracle_rj(U[0], U[1], U[2], ui5)
+                                + (g_mutation == 2 ? -1.0 : 1.0) * oracle_rc(s52, qi5));
     cplx dij = r[j] - r[i], dik = r[k] - r[i];
     cplx sumr = r[0] + r[1] + r[2] + 3.0;
-    cplx Xd = Om_h * 2.0 * z / 3.0 *
-              ((X[0] * X[1] * X[2] - Y[0] * Y[1] * Y[2]) / z
+    cplx Xd = Om_h * 2.0 * dz / 3.0 *
+              ((X[0] * X[1] * X[2] - Y[0] * Y[1] * Y[2]) / dz
                + (3.0 * (r[i] + 1.0) * (r[i] + 1.0) - dij * dik) * rf
-               + 2.0 * sumr * (z * z / 3.0 * dij * dik * oracle_rd(U[j], U[k], U[i])
+               + 2.0 * sumr * (dz * dz / 3.0 * dij * dik * oracle_rd(U[j], U[k], U[i])
                                + Y[i] * X[i] / u[i]));
     res[0] = creal(chi); im[0] = cimag(chi);
     res[1] = creal(t); im[1] = cimag(t);
     res[2] = creal(Xd); im[2] = cimag(Xd);
 }
 
-/* O2 batch.  roots [B][4] complex (re,im) of E^2 in x = 1+z (Sec. 3, eq. 3.2;
- * m = nroot[b] = 4 or 3 entries used); perm [B][3] = (i_t, i_X, l_X).
- * out [nnz][6] as in oracle_quad_distances; imag [nnz][3] imaginary parts. */
-int oracle_carlson_distances(const double* params, int64_t B, int ncol, const int64_t* offsets,
-                             const double* z, int64_t nnz, const double* roots,
-                             const int32_t* nroot, const int32_t* perm, double* out,
-                             double* imag) {
+/* The z2 -> infinity limits of eqs. (3.7) and (3.8) (quartic, index i = it
+ * for t).  With X_m ~ sqrt(z2) every u_ab grows like Delta z, and
+ *   U_ab = lim u_ab / Delta z = Y_c Y_d + Y_a Y_b
+ * ({c,d} the complement of {a,b}); R_F and R_C are homogeneous of degree
+ * -1/2 and R_J of degree -3/2, so every Delta z prefactor cancels:
+ *   chi(z1, inf) = Or^-1/2 2 R_F(U_12^2, U_13^2, U_14^2),
+ *   t(z1, inf)   = Or^-1/2 2/(r_i+1) { R_F - [ d_ij d_ik d_il/(3 d_i5)
+ *                  R_J(..., U_i5^2) + R_C(S_i5^2, Q_i5^2) ] },
+ *   U_i5^2 = U_ij^2 - d_ik d_il d_j5/d_i5,  Q_i5^2 = (z1+1)/(z1-r_i) U_i5^2,
+ *   S_i5^2 = Q_i5^2 + d_k5 d_l5 d_j5/d_i5.
+ * res[2] = (chi, t) in units of c/H0 and 1/H0. */
+static void quartic_carlson_inf(const cplx* r, double Or, double z1, int it, double* res, double* im) {
+    cplx Y[4];
+    for (int m = 0; m < 4; m++) Y[m] = lower_root(z1, r[m]);
+#define UINF(a, b, out) do { int cc_ = -1, dd_ = -1; \
+        for (int m_ = 0; m_ < 4; m_++) if (m_ != (a) && m_ != (b)) { if (cc_ < 0) cc_ = m_; else dd_ = m_; } \
+        out = Y[cc_] * Y[dd_] + Y[a] * Y[b]; } while (0)
+    double Or_h = 1.0 / sqrt(Or);
+    cplx u12, u13, u14;
+    UINF(0, 1, u12); UINF(0, 2, u13); UINF(0, 3, u14);
+    cplx chi = Or_h * 2.0 * oracle_rf(u12 * u12, u13 * u13, u14 * u14);
+    int i = it, o[3], n = 0;
+    for (int m = 0; m < 4; m++) if (m != i) o[n++] = m;
+    int j = o[0], k = o[1], l = o[2];
+    cplx uij, uik, uil;
+    UINF(i, j, uij); UINF(i, k, uik); UINF(i, l, uil);
+    cplx U0 = uij * uij, U1 = uik * uik, U2 = uil * uil;
+    cplx dij = r[j] - r[i], dik = r[k] - r[i], dil = r[l] - r[i];
+    cplx di5 = -(1.0 + r[i]), dj5 = -(1.0 + r[j]), dk5 = -(1.0 + r[k]), dl5 = -(1.0 + r[l]);
+    cplx ui5 = U0 - dik * dil * dj5 / di5;
+    cplx qi5 = (z1 + 1.0) / (z1 - r[i]) * ui5;
+    cplx si5 = qi5 + dk5 * dl5 * dj5 / di5;
+    if (fabs(cimag(ui5)) <= 1e-13 * cabs(ui5)) ui5 = creal(ui5);
+    if (fabs(cimag(qi5)) <= 1e-13 * cabs(qi5)) qi5 = creal(qi5);
+    if (fabs(cimag(si5)) <= 1e-13 * cabs(si5)) si5 = creal(si5);
+    cplx br = dij * dik * dil / (3.0 * di5) * oracle_rj(U0, U1, U2, ui5)
+              + (g_mutation == 8 ? 0.0 : 1.0) * oracle_rc(si5, qi5);
+    cplx t = Or_h * 2.0 / (r[i] + 1.0) * (oracle_rf(U0, U1, U2) - br);
+    res[0] = creal(chi); im[0] = cimag(chi);
+    res[1] = creal(t); im[1] = cimag(t);
+#undef UINF
+}
+
+/* The z2 -> infinity limits of eqs. (B.1) and (B.2).  Here u_i / Delta z ->
+ * Y_i, so U_i^2 = z1 - r_i and U_i5^2 = U_i^2 + (r_i + 1) = 1 + z1; the R_C
+ * term of (B.2) falls off like Delta z^-1/2 and vanishes:
+ *   chi(z1, inf) = Om^-1/2 2 R_F(z1 - r_1, z1 - r_2, z1 - r_3),
+ *   t(z1, inf)   = Om^-1/2 (2/3) R_J(z1 - r_1, z1 - r_2, z1 - r_3, 1 + z1). */
+static void cubic_carlson_inf(const cplx* r, double Om, double z1, int i, double* res, double* im) {
+    cplx Y[3], U[3];
+    for (int m = 0; m < 3; m++) { Y[m] = lower_root(z1, r[m]); U[m] = Y[m] * Y[m]; }
+    double Om_h = 1.0 / sqrt(Om);
+    cplx chi = Om_h * 2.0 * oracle_rf(U[0], U[1], U[2]);
+    cplx ui5 = U[i] + (r[i] + 1.0);
+    if (fabs(cimag(ui5)) <= 1e-13 * cabs(ui5)) ui5 = creal(ui5);
+    cplx t = Om_h * 2.0 / 3.0 * oracle_rj(U[0], U[1], U[2], ui5);
+    res[0] = creal(chi); im[0] = cimag(chi);
+    res[1] = creal(t); im[1] = cimag(t);
+}
+
+static void unpack_roots(const double* roots, int64_t b, int m, cplx* r) {
+    for (int a = 0; a < m; a++) r[a] = (roots[8 * b + 2 * a] - 1.0) + I * roots[8 * b + 2 * a + 1];
+}
+
+/* O2 batch with general limits.  roots [B][4] complex (re,im) of E^2 in
+ * x = 1+z (Sec. 3, eq. 3.2; m = nroot[b] = 4 or 3 entries used); perm [B][3]
+ * = (i_t, i_X, l_X); z1 [B] lower limits (NULL: 0), z2 [nnz] upper limits.
+ * out [nnz][6] as in quad_pair; imag [nnz][3] imaginary parts. */
+int oracle_carlson_between(const double* params, int64_t B, int ncol, const int64_t* offsets,
+                           const double* z1v, const double* z, int64_t nnz, const double* roots,
+                           const int32_t* nroot, const int32_t* perm, double* out, double* imag) {
     for (int64_t j = 0; j < nnz; j++) {
         int64_t b = row_of(offsets, B, nnz, j);
         double H0;
         cosmo_t c;
         unpack_params(params + b * ncol, ncol, &H0, &c);
-        double zz = z[j], DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0;
+        double z1 = z1v ? z1v[b] : 0.0, zz = z[j], DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0;
+        double* o = out + 6 * j;
+        if (!(zz >= z1)) {
+            for (int k = 0; k < 6; k++) o[k] = NAN;
+            if (imag) for (int k = 0; k < 3; k++) imag[3 * j + k] = NAN;
+            continue;
+        }
         int m = nroot[b];
         cplx r[4];
-        for (int a = 0; a < m; a++)
-            r[a] = (roots[8 * b + 2 * a] - 1.0) + I * roots[8 * b + 2 * a + 1];
+        unpack_roots(roots, b, m, r);
         double res[3] = {0, 0, 0}, im[3] = {0, 0, 0};
-        if (zz != 0.0) {
+        if (zz != z1) {
             if (m == 4)
-                quartic_carlson(r, c.Or, zz, perm[3 * b], perm[3 * b + 1], perm[3 * b + 2], res, im);
+                quartic_carlson(r, c.Or, z1, zz, perm[3 * b], perm[3 * b + 1], perm[3 * b + 2], res, im);
             else
-                cubic_carlson(r, c.Om, zz, perm[3 * b + 1], res, im);
+                cubic_carlson(r, c.Om, z1, zz, perm[3 * b + 1], res, im);
         }
         double S, SD, Sk;
         curv_map(res[0], c.Ok, &S, &SD, &Sk);
-        double* o = out + 6 * j;
         o[0] = DH * res[0]; o[1] = tH * res[1]; o[2] = DH * res[2];
         o[3] = DH * S;
-        o[4] = (g_mutation == 4 ? 1.0 : 1.0 + zz) * o[3];
+        o[4] = (g_mutation == 4 ? 1.0 : 1.0 + zz) / ((1.0 + z1) * (1.0 + z1)) * o[3];
         o[5] = 5.0 * log10(o[4]) + 25.0;
         if (imag) { imag[3 * j] = DH * im[0]; imag[3 * j + 1] = tH * im[1]; imag[3 * j + 2] = DH * im[2]; }
+    }
+    return 0;
+}
+
+/* O2 with z1 = 0, z2 = z for every pair. */
+int oracle_carlson_distances(const double* params, int64_t B, int ncol, const int64_t* offsets,
+                             const double* z, int64_t nnz, const double* roots,
+                             const int32_t* nroot, const int32_t* perm, double* out,
+                             double* imag) {
+    return oracle_carlson_between(params, B, ncol, offsets, NULL, z, nnz, roots, nroot, perm, out, imag);
+}
+
+/* O2 limits z2 -> infinity per row: out [B][2] = (chi(z1, inf) [Mpc],
+ * t(z1, inf) [Gyr]); imag [B][2] imaginary parts (may be NULL). */
+int oracle_carlson_limits(const double* params, int64_t B, int ncol, const double* z1v, const double* roots,
+                          const int32_t* nroot, const int32_t* perm, double* out, double* imag) {
+    for (int64_t b = 0; b < B; b++) {
+        double H0;
+        cosmo_t c;
+        unpack_params(params + b * ncol, ncol, &H0, &c);
+        int m = nroot[b];
+        cplx r[4];
+        unpack_roots(roots, b, m, r);
+        double res[2], im[2];
+        if (m == 4)
+            quartic_carlson_inf(r, c.Or, z1v[b], perm[3 * b], res, im);
+        else
+            cubic_carlson_inf(r, c.Om, z1v[b], perm[3 * b + 1], res, im);
+        out[2 * b] = C_KMS / H0 * res[0];
+        out[2 * b + 1] = HUBBLE_TIME_GYR / H0 * res[1];
+        if (imag) { imag[2 * b] = C_KMS / H0 * im[0]; imag[2 * b + 1] = HUBBLE_TIME_GYR / H0 * im[1]; }
     }
     return 0;
 }

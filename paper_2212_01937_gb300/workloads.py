@@ -190,3 +190,34 @@ def precision_stress(B=10_000, n=10_000, seed=4):
         z[b] = 10.0 ** rng.uniform(-4.0, np.log10(1100.0), n)
     return Batch("stress-%dx%d" % (B, n), params, z.reshape(-1),
                  np.arange(B + 1, dtype=np.int64) * n)
+
+
+def between_batch(B=4096, n=1024, seed=5, z1max=3.0, dzmax=10.0):
+    """General limits: cosmologies as general_batch; per row a lower limit
+    z1 ~ U(0, z1max) (an observer, lens or absorber redshift), then n upper
+    limits z2 = z1 + dz, dz ~ U(0, dzmax).  extra["z1"] holds z1 [B]."""
+    rng = np.random.default_rng(seed)
+    params = np.zeros((B, 4))
+    z1 = np.zeros(B)
+    z = np.zeros((B, n))
+    for b in range(B):
+        H0, Om, OL, Or = _draw_cosmo(rng)
+        params[b] = (H0, Om, OL, Or)
+        z1[b] = rng.uniform(0.0, z1max)
+        z[b] = z1[b] + rng.uniform(0.0, dzmax, n)
+    return Batch("between-%dx%d" % (B, n), params, z.reshape(-1),
+                 np.arange(B + 1, dtype=np.int64) * n, extra={"z1": z1})
+
+
+def limits_batch(B=65536, seed=6):
+    """Upper limit at infinity (age, horizon): cosmologies as general_batch,
+    one lower limit per row, half z1 ~ U(0, 10) and half z1 ~ logU(10, 1100)."""
+    rng = np.random.default_rng(seed)
+    params = np.zeros((B, 4))
+    z1 = np.zeros(B)
+    for b in range(B):
+        H0, Om, OL, Or = _draw_cosmo(rng)
+        params[b] = (H0, Om, OL, Or)
+        z1[b] = rng.uniform(0.0, 10.0) if b % 2 == 0 else 10.0 ** rng.uniform(1.0, np.log10(1100.0))
+    return Batch("limits-%d" % B, params, np.zeros(0), np.zeros(B + 1, dtype=np.int64),
+                 extra={"z1": z1})
