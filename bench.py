@@ -142,6 +142,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="use the default launch shape")
     ap.add_argument("--no-vi", action="store_true", help="skip the variational-inference step timing")
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged log-likelihood step timing")
+    ap.add_argument("--no-limits", action="store_true",
+                    help="skip the general-limits and age/horizon timings")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -268,6 +270,9 @@ def main():
             line["vi_step"] = vi_step_rate(dev)
         if not args.no_ragged:
             line["ragged_step"] = ragged_step_rate(dev)
+        if not args.no_limits:
+            line["between_step"] = between_step_rate(dev)
+            line["limits_step"] = limits_rate(dev)
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -351,6 +356,42 @@ def ragged_step_rate(dev, steps=10):
     ms = graph_ms(lambda: lcdm.gauss_loglike(params, z, m, off, M=d.M, sigma=d.sigma, call=call), dev, reps=steps)
     return {"workload": d.name + " (16384 cosmologies x floor(10^U(0,5)) z, CSR), FP32, CUDA-graph replay",
             "pairs_per_step": int(d.nnz), "ms_per_step": ms, "value": d.nnz / (ms / 1e3), "unit": UNIT}
+
+
+def between_step_rate(dev):
+    """Fused forward + adjoint with general lower limits: 4096 rows, each with
+    its own z1 ~ U(0, 3) and 1024 upper limits z2 = z1 + U(0, 10), FP32,
+    cotangents on d_C, t, X, mu (the per-row shift, root preparation, pair
+    maps, pair kernel and gradient chain rule), replayed from a CUDA graph."""
+    import torch
+    from paper_2212_01937_gb300 import lcdm, workloads
+    d = workloads.between_batch()
+    params = torch.tensor(d.params, device=dev)
+    off = torch.tensor(d.offsets, device=dev)
+    z1 = torch.tensor(d.extra["z1"], device=dev)
+    z = torch.tensor(d.z, dtype=torch.float32).to(dev)
+    g = torch.Generator(device="cpu").manual_seed(11)
+    cot = {n: torch.randn(d.nnz, generator=g).to(dev) for n in OUTPUTS}
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    f = lambda: lcdm.distances_between(params, z1, z, off, outputs=OUTPUTS, cot=cot, precision="fp32")
+    ms = graph_ms(lambda: (flush.zero_(), f()), dev) - graph_ms(lambda: flush.zero_(), dev)
+    return {"workload": d.name + " (z1 ~ U(0,3) per row, z2 = z1 + U(0,10)), FP32 fused VJP, "
+                                 "CUDA-graph replay, L2 flushed",
+            "pairs_per_step": int(d.nnz), "ms_per_step": ms, "value": d.nnz / (ms / 1e3), "unit": UNIT}
+
+
+def limits_rate(dev):
+    """Age t(z1, inf) and comoving horizon chi(z1, inf) with their gradient,
+    65536 rows (z1 half U(0, 10), half logU(10, 1100)), FP64, CUDA-graph replay."""
+    import torch
+    from paper_2212_01937_gb300 import lcdm, workloads
+    d = workloads.limits_batch()
+    params = torch.tensor(d.params, device=dev)
+    z1 = torch.tensor(d.extra["z1"], device=dev)
+    cc = torch.ones(d.B, dtype=torch.float64, device=dev)
+    ms = graph_ms(lambda: lcdm.limits(params, z1, cot_chi=cc, cot_t=cc, grad=True), dev)
+    return {"workload": d.name + " rows, age + horizon + gradient, FP64, CUDA-graph replay",
+            "rows_per_step": d.B, "ms_per_step": ms, "value": d.B / (ms / 1e3), "unit": "rows/s"}
 
 
 def fp64_baselines(lcdm, params, offsets, b, dev):

@@ -3,7 +3,8 @@
  * (cosmology, redshift) pairs on one GB300 (sm_103a), after Karchev,
  * "Analytic auto-differentiable LambdaCDM cosmography" (arXiv:2212.01937).
  *
- * What is computed (z1 = 0, z2 = z for every pair):
+ * What is computed (z1 = 0, z2 = z for every pair; lcdm_distances_between
+ * and lcdm_limits below take general lower limits and z2 = infinity):
  *   comoving distance  d_C = chi(0, z)                eq. (2.3), via eq. (3.7)/(B.1)
  *   time coordinate    t   = t(0, z) (lookback time)  eq. (2.4), via eq. (3.8)/(B.2)
  *   absorption dist.   X   = d_abs(0, z)              eq. (2.5), via eq. (3.9)/(B.3)
@@ -217,6 +218,65 @@ lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offset
                           int32_t* cosmo_status, const lcdm_opts* opts, void* ws, size_t ws_bytes,
                           cudaStream_t stream, int32_t* best_block, int32_t* best_blocks_per_sm,
                           float* best_ms, int32_t* best_lane_map);
+
+/* ---------------------------------------------------------------------------
+ * General limits.  Eqs. (2.3)-(2.5) are integrals from z1 to z2; the entry
+ * points above take z1 = 0.  The two below take a lower limit z1[b] >= 0 per
+ * row (device, float64).  They evaluate eqs. (3.7)-(3.9) / (B.1)-(B.3) with
+ * X_m = sqrt(z2 - r_m), Y_m = sqrt(z1 - r_m), Delta z = z2 - z1 (Sec. 3.1) in
+ * the form they take in the coordinate of an observer at z1: with s = 1 + z1
+ * and E1 = E^2(z1), the row becomes the closed cosmology
+ *   (H0 sqrt(E1), Om s^3/E1, OL/E1, Or s^4/E1), Ok' = Ok s^2/E1 by closure,
+ * with roots (r - z1)/s, the pair's upper limit becomes (z2 - z1)/s, and
+ * every output is the z1 = 0 result of that cosmology times a power of s.
+ * The root preparation therefore runs once per row (on the shifted
+ * parameters) and cosmo_status refers to the shifted cosmology: status 1 means
+ * a real root of E^2 at z >= z1; status 2 also covers z1 < 0, non-finite z1
+ * or E^2(z1) <= 0.
+ * ------------------------------------------------------------------------- */
+
+/* Workspace bytes of lcdm_distances_between (B rows, n as in the layout) and
+ * of lcdm_limits (n = 0).                                                   */
+lcdm_status lcdm_between_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts, size_t* bytes);
+
+/* Distances between z1[b] and each pair's z2 (layouts LCDM_LAYOUT_CSR and
+ * LCDM_LAYOUT_DENSE; SHARED is rejected), with the fused adjoint when grad is
+ * not NULL.  Per pair, in the output slots of the z1 = 0 entry points:
+ *   LCDM_DC  chi(z1, z2)                        eq. (2.3), via (3.7)/(B.1)
+ *   LCDM_T   t(z1, z2)                          eq. (2.4), via (3.8)/(B.2)
+ *   LCDM_X   d_abs(z1, z2)                      eq. (2.5), via (3.9)/(B.3)
+ *   LCDM_DM  transverse comoving distance S_k(chi(z1, z2)), today's units
+ *   LCDM_DL  (1+z2) d_M / (1+z1)^2: the luminosity distance of a source at
+ *            z2 seen by a comoving observer at z1 (its redshift relative to
+ *            that observer is (1+z2)/(1+z1) - 1)
+ *   LCDM_MU  5 log10(d_L / 10 pc)
+ * With z1 = 0 these are the outputs of lcdm_distances.  Domain z2 >= z1:
+ * pairs with z2 < z1 give NaN outputs and add nothing to the gradient; z2 = z1
+ * gives 0 (mu = -inf).
+ *   cot, grad: as lcdm_distances_vjp (cot required when grad is not NULL;
+ *   grad NULL computes the forward outputs only).  out may be NULL when grad
+ *   is not, and its entries may be NULL.
+ *   ws: lcdm_between_workspace_size(B, n, opts) bytes, 256-byte aligned.
+ * Precision, units, streams and errors as above.                            */
+lcdm_status lcdm_distances_between(const double* params, int64_t B, const double* z1, const int64_t* offsets,
+                                   const void* z2, int64_t n, const void* const cot[LCDM_NOUT],
+                                   void* const out[LCDM_NOUT], double* grad, int32_t* cosmo_status,
+                                   const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
+
+/* The upper limit at infinity, per row (Sec. 2.1.1: the age of the universe
+ * at z1 is t(z1, inf)):
+ *   chi_inf [B]  chi(z1, inf) [Mpc], the comoving distance to the particle
+ *                horizon (limit of eq. 3.7 / B.1)
+ *   t_inf   [B]  t(z1, inf) [Gyr], the age at redshift z1 (limit of eq. 3.8 /
+ *                B.2); at z1 = 0 the present age of the universe
+ * (d_abs diverges).  Either may be NULL.  Always FP64 (float64 arrays,
+ * whatever opts->precision).  With grad not NULL, grad[b][c] =
+ * cot_chi[b] d chi_inf / d params[b][c] + cot_t[b] d t_inf / d params[b][c]
+ * (a NULL cotangent counts as zero).  opts->layout is ignored.
+ *   ws: lcdm_between_workspace_size(B, 0, opts) bytes, 256-byte aligned.    */
+lcdm_status lcdm_limits(const double* params, int64_t B, const double* z1, double* chi_inf, double* t_inf,
+                        const double* cot_chi, const double* cot_t, double* grad, int32_t* cosmo_status,
+                        const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
 
 /* Human-readable name of a lcdm_status value (static string). */
 const char* lcdm_status_string(int status);

@@ -7,6 +7,7 @@
 #include <tuple>
 
 #include "../../include/lcdm.h"
+#include "lcdm_between.cuh"
 #include "lcdm_launch.cuh"
 #include "lcdm_prep.cuh"
 
@@ -307,9 +308,164 @@ HostCarve host_carve(char* base, int64_t B, int64_t n, int ncol, size_t es) {
     return c;
 }
 
+// Device workspace of the general-limits entry points: records of the
+// shifted cosmologies, shifted parameters (closure form, four columns), their
+// Jacobian, the scale s = 1+z1,
+// the gradient w.r.t. the shifted parameters, z' and three scaled cotangents
+// (d_C, X, d_M).
+struct BetweenCarve {
+    Carved rec;
+    double* params4;
+    double* jac;
+    double* scale;
+    double* gradp;
+    char* zp;
+    char* cotp[LCDM_NOUT];
+    size_t bytes;
+};
+
+BetweenCarve between_carve(char* base, int64_t B, int64_t npairs, int ncol, size_t es) {
+    BetweenCarve c;
+    size_t off = 0;
+    auto take = [&](size_t bytes) { char* p = base ? base + off : nullptr; off += align256(bytes); return p; };
+    char* rec = take(ws_bytes_for(B));
+    c.rec.recD = (double*)rec;
+    c.rec.recF = rec ? (float2*)(rec + align256((size_t)B * NREC * sizeof(double))) : nullptr;
+    c.params4 = (double*)take((size_t)B * 4 * sizeof(double));
+    c.jac = (double*)take((size_t)B * 4 * ncol * sizeof(double));
+    c.scale = (double*)take((size_t)B * sizeof(double));
+    c.gradp = (double*)take((size_t)B * 4 * sizeof(double));
+    c.zp = take((size_t)npairs * es);
+    for (int i = 0; i < LCDM_NOUT; i++) c.cotp[i] = nullptr;
+    c.cotp[LCDM_DC] = take((size_t)npairs * es);
+    c.cotp[LCDM_X] = take((size_t)npairs * es);
+    c.cotp[LCDM_DM] = take((size_t)npairs * es);
+    c.bytes = off;
+    return c;
+}
+
+lcdm_status between_npairs(int64_t B, int64_t n, const lcdm_opts* opts, int64_t* npairs) {
+    if (!opts_ok(opts) || B <= 0 || n < 0 || (n > 0 && opts->layout == LCDM_LAYOUT_SHARED))
+        return LCDM_ERR_INVALID;
+    *npairs = opts->layout == LCDM_LAYOUT_CSR ? n : B * n;
+    return LCDM_OK;
+}
+
+// Shift every row to its lower limit and prepare the shifted records.
+lcdm_status between_setup(const double* params, int64_t B, const double* z1, int ncol, const BetweenCarve& w,
+                          const lcdm_opts* opts4, int32_t* status, double* gradp, cudaStream_t stream) {
+    ShiftArgs sa;
+    sa.params = params;
+    sa.z1 = z1;
+    sa.B = B;
+    sa.ncol = ncol;
+    sa.params4 = w.params4;
+    sa.jac = w.jac;
+    sa.scale = w.scale;
+    if (launch_shift(sa, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+    g_launches++;
+    return run_prep(w.params4, B, opts4, w.rec, status, gradp, nullptr, stream);
+}
+
 }  // namespace
 
 extern "C" {
+
+lcdm_status lcdm_between_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts, size_t* bytes) {
+    int64_t npairs = 0;
+    if (!bytes || between_npairs(B, n, opts, &npairs) != LCDM_OK) return LCDM_ERR_INVALID;
+    const size_t es = opts->precision == LCDM_FP64 ? 8 : 4;
+    *bytes = between_carve(nullptr, B, npairs, opts->ncol, es).bytes;
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_distances_between(const double* params, int64_t B, const double* z1, const int64_t* offsets,
+                                   const void* z2, int64_t n, const void* const cot[LCDM_NOUT],
+                                   void* const out[LCDM_NOUT], double* grad, int32_t* cosmo_status,
+                                   const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    int64_t npairs = 0;
+    if (between_npairs(B, n, opts, &npairs) != LCDM_OK || !z1 || (!out && !grad) || (grad && !cot))
+        return LCDM_ERR_INVALID;
+    lcdm_status st = check_pairs_args(params, B, offsets, z2, n, cosmo_status, opts);
+    if (st != LCDM_OK) return st;
+    const int ncol = opts->ncol;
+    const size_t es = opts->precision == LCDM_FP64 ? 8 : 4;
+    if (!ws || ((uintptr_t)ws & 255) != 0) return LCDM_ERR_WORKSPACE;
+    BetweenCarve w = between_carve((char*)ws, B, npairs, ncol, es);
+    if (ws_bytes < w.bytes) return LCDM_ERR_WORKSPACE;
+    lcdm_opts o4 = *opts;
+    o4.ncol = 4;
+    st = between_setup(params, B, z1, ncol, w, &o4, cosmo_status, grad ? w.gradp : nullptr, stream);
+    if (st != LCDM_OK) return st;
+    PairMapArgs m;
+    memset(&m, 0, sizeof(m));
+    m.offsets = opts->layout == LCDM_LAYOUT_CSR ? offsets : nullptr;
+    m.nrow = n;
+    m.nnz = npairs;
+    m.B = B;
+    m.fp64 = opts->precision == LCDM_FP64;
+    m.z1 = z1;
+    m.scale = w.scale;
+    m.z2 = z2;
+    m.zp = w.zp;
+    const void* cotk[LCDM_NOUT] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    if (grad)
+        for (int i = 0; i < LCDM_NOUT; i++) {
+            m.cot[i] = cot[i];
+            cotk[i] = cot[i];
+            if (cot[i] && w.cotp[i]) { m.cotp[i] = w.cotp[i]; cotk[i] = w.cotp[i]; }
+        }
+    if (launch_pair_pre(m, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+    g_launches++;
+    Plan P;
+    make_plan(w.params4, B, offsets, w.zp, n, out, nullptr, grad ? cotk : nullptr, nullptr, 0, 1,
+              grad ? w.gradp : nullptr, nullptr, cosmo_status, &o4, w.rec, P);
+    st = launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
+    if (st != LCDM_OK) return st;
+    if (out) {
+        for (int i = 0; i < LCDM_NOUT; i++) m.out[i] = out[i];
+        if (launch_pair_post(m, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+        g_launches++;
+    }
+    if (grad) {
+        if (launch_chain(w.jac, w.gradp, B, ncol, grad, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+        g_launches++;
+    }
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_limits(const double* params, int64_t B, const double* z1, double* chi_inf, double* t_inf,
+                        const double* cot_chi, const double* cot_t, double* grad, int32_t* cosmo_status,
+                        const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!opts_ok(opts) || B <= 0 || !params || !z1 || !cosmo_status || (!chi_inf && !t_inf && !grad))
+        return LCDM_ERR_INVALID;
+    const int ncol = opts->ncol;
+    if (!ws || ((uintptr_t)ws & 255) != 0) return LCDM_ERR_WORKSPACE;
+    BetweenCarve w = between_carve((char*)ws, B, 0, ncol, 8);
+    if (ws_bytes < w.bytes) return LCDM_ERR_WORKSPACE;
+    lcdm_opts o4 = *opts;
+    o4.ncol = 4;
+    lcdm_status st = between_setup(params, B, z1, ncol, w, &o4, cosmo_status, nullptr, stream);
+    if (st != LCDM_OK) return st;
+    LimitArgs la;
+    la.recD = w.rec.recD;
+    la.recF = w.rec.recF;
+    la.status = cosmo_status;
+    la.B = B;
+    la.scale = w.scale;
+    la.chi = chi_inf;
+    la.age = t_inf;
+    la.cot_chi = cot_chi;
+    la.cot_age = cot_t;
+    la.gradp = w.gradp;
+    if (launch_limits(la, grad != nullptr, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+    g_launches++;
+    if (grad) {
+        if (launch_chain(w.jac, w.gradp, B, ncol, grad, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+        g_launches++;
+    }
+    return LCDM_OK;
+}
 
 lcdm_status lcdm_distances_static(const double* params, int64_t B, const int64_t* offsets, const void* z,
                                   int64_t n, void* const out[LCDM_NOUT], int32_t* cosmo_status,

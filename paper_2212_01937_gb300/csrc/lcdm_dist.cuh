@@ -398,4 +398,58 @@ LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, 
     }
 }
 
+// ------------------------------------------------------ z -> infinity ------
+// The upper limit at infinity (Sec. 2.1.1: the age t(0, inf); the comoving
+// distance to the particle horizon chi(0, inf)) of the quantities above, with
+// the same root labels and scalings.  As z grows, n_j / sqrt(z) -> sqrt(q_j),
+// every u grows like z, and with the homogeneity of R_F, R_C (degree -1/2)
+// and R_J (degree -3/2) every power of z cancels; in eq. (3.8)
+// (1+z) / (1 + eps_A (1+z)) -> 1 / eps_A.  In (B.2) the R_C term falls off
+// like z^-1/2 and drops out.  Ichi and It are in the units of their
+// finite-z counterparts (c/H0 and 1/H0 after the record's prefactors).
+template <class S, class PS>
+LCDM_NI void quartic_limits(const S& mA, const S& epsA, const S& B, const PS& P, const S& qA, const S& qB,
+                            const PS& qP, const S& nrm, S& Ichi, S& It, int* fail) {
+    typedef typename Base<S>::type T;
+    const T one = cst<T>(1.0), third = cst<T>(1.0 / 3.0);
+    S nA = ssqrt(qA), nB = ssqrt(qB);
+    PS nP = psqrt(qP);
+    S uAB = nrm * (nA * nB + pprod(nP));
+    PS uAP = pscale(pscale(nP, nA) + pscale(pswap(nP), nB), nrm);
+    S x1 = uAB * uAB;
+    PS pr = uAP * uAP;
+    S rhoB = B + one;
+    PS rhoP = padd(P, one);
+    S ppPA = pprod(padd(pscale(rhoP, epsA), one));
+    S p[1];
+    p[0] = -(mA * ppPA * rhoB);
+    S RF, RD1, RJ[1];
+    carlson_any<1, false, false>(x1, pr, p, RF, RD1, RJ, fail);
+    Ichi = RF * cst<T>(2.0);                                   // eq. (3.7), z -> inf
+    S kq5 = (x1 + p[0]) / ((one + epsA) * epsA);
+    S ks5 = kq5 + mA * pprod(rhoP) * rhoB;
+    It = (rc_any(ks5, kq5, fail) - epsA * RF - mA * (one + epsA * rhoB) * ppPA * RJ[0] * third)
+         * cst<T>(2.0);                                        // eq. (3.8), z -> inf
+}
+
+template <class S, class PS>
+LCDM_NI void cubic_limits(const S& A, const S& amh, const S& qA, const PS& qP, const S& nrm, S& Ichi, S& It,
+                          int* fail) {
+    typedef typename Base<S>::type T;
+    const T one = cst<T>(1.0);
+    S nA = ssqrt(qA);
+    PS nP = psqrt(qP);
+    // u_A / z -> N n_P n_P*,  u_P / z -> N n_P* n_A  (the plain u_i -> Y_i = sqrt(-r_i))
+    S uA = nrm * pprod(nP);
+    PS uP = pscale(pswap(nP), nA * nrm);
+    S x1 = uA * uA;
+    PS pr = uP * uP;
+    S p[1];
+    p[0] = A + one;                                            // u_A5^2 - u_A^2 = rho_A
+    S RF, RD1, RJ[1];
+    carlson_any<1, false, false>(x1, pr, p, RF, RD1, RJ, fail);
+    Ichi = amh * RF * cst<T>(2.0);                             // eq. (B.1), z -> inf
+    It = amh * RJ[0] * cst<T>(2.0 / 3.0);                      // eq. (B.2), z -> inf
+}
+
 }  // namespace lcdm

@@ -57,12 +57,16 @@ def load():
     lib.lcdm_autotune.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp,
                                   ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(ctypes.c_float),
                                   ctypes.POINTER(i32)]
+    lib.lcdm_between_workspace_size.argtypes = [i64, i64, op, ctypes.POINTER(sz)]
+    lib.lcdm_distances_between.argtypes = [_vp, i64, _vp, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp]
+    lib.lcdm_limits.argtypes = [_vp, i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, op, _vp, sz, _vp]
     lib.lcdm_status_string.argtypes = [ctypes.c_int]
     lib.lcdm_status_string.restype = ctypes.c_char_p
     lib.lcdm_launch_count.restype = i64
     for f in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
               "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_host_workspace_size",
-              "lcdm_distances_vjp_host"):
+              "lcdm_distances_vjp_host", "lcdm_between_workspace_size", "lcdm_distances_between",
+              "lcdm_limits"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -195,6 +199,64 @@ def distances_vjp(params, z, cot, offsets=None, outputs=(), call=None, **kw):
     out["grad"] = grad
     out["status"] = c.status
     return out
+
+
+def _between_ws(c, n):
+    nbytes = ctypes.c_size_t()
+    _check(load().lcdm_between_workspace_size(c.B, n, ctypes.byref(c.opts), ctypes.byref(nbytes)))
+    return torch.empty(max(nbytes.value, 1), dtype=torch.uint8, device=c.device)
+
+
+def distances_between(params, z1, z2, offsets=None, outputs=("d_C", "t", "X", "mu"), cot=None, **kw):
+    """Eqs. (2.3)-(2.5) from z1[b] (per row) to each pair's z2
+    (lcdm_distances_between); with ``cot`` ({name: [npairs]}) also the fused
+    adjoint, returned as "grad" [B, ncol].  d_L and mu are those of a source
+    at z2 seen by a comoving observer at z1.  Layouts "csr" and "dense"."""
+    c = Call(params, z2, offsets, **kw)
+    if c.layout == "shared":
+        raise ValueError("general limits need the csr or dense layout")
+    z1d = torch.as_tensor(z1, dtype=torch.float64).to(c.device).reshape(-1).contiguous()
+    if z1d.numel() != c.B:
+        raise ValueError("z1 must hold one lower limit per row")
+    ws = _between_ws(c, c.n)
+    out, vp = c.out_buffers(outputs)
+    cp, grad = _VP6(), None
+    if cot is not None:
+        cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items() if v is not None}
+        cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])
+        grad = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device)
+    _check(load().lcdm_distances_between(_ptr(c.params), c.B, _ptr(z1d), _ptr(c.offsets), _ptr(c.z), c.n, cp,
+                                         vp, _ptr(grad), _ptr(c.status), ctypes.byref(c.opts), _ptr(ws),
+                                         ws.numel(), _stream(c.device)))
+    if grad is not None:
+        out["grad"] = grad
+    out["status"] = c.status
+    return out
+
+
+def limits(params, z1, cot_chi=None, cot_t=None, grad=False, **kw):
+    """The upper limit at infinity per row (lcdm_limits): "chi_inf" [B] (Mpc,
+    comoving distance to the particle horizon from z1) and "t_inf" [B] (Gyr,
+    the age at z1), FP64; with grad, "grad" [B, ncol] of
+    sum_b cot_chi[b] chi_inf[b] + cot_t[b] t_inf[b]."""
+    kw.setdefault("precision", "fp64")
+    c = Call(params, torch.zeros(params.shape[0], device=params.device), layout="dense", **kw)
+    z1d = torch.as_tensor(z1, dtype=torch.float64).to(c.device).reshape(-1).contiguous()
+    if z1d.numel() != c.B:
+        raise ValueError("z1 must hold one lower limit per row")
+    ws = _between_ws(c, 0)
+    f64 = dict(dtype=torch.float64, device=c.device)
+    chi = torch.empty(c.B, **f64)
+    age = torch.empty(c.B, **f64)
+    g = torch.empty(c.B, c.ncol, **f64) if grad else None
+    cc = None if cot_chi is None else torch.as_tensor(cot_chi, **f64).reshape(-1).contiguous()
+    ct = None if cot_t is None else torch.as_tensor(cot_t, **f64).reshape(-1).contiguous()
+    _check(load().lcdm_limits(_ptr(c.params), c.B, _ptr(z1d), _ptr(chi), _ptr(age), _ptr(cc), _ptr(ct), _ptr(g),
+                              _ptr(c.status), ctypes.byref(c.opts), _ptr(ws), ws.numel(), _stream(c.device)))
+    res = {"chi_inf": chi, "t_inf": age, "status": c.status}
+    if grad:
+        res["grad"] = g
+    return res
 
 
 class HostVJP:

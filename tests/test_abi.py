@@ -30,7 +30,7 @@ def test_header_declares_entry_points():
     syms = declared_symbols()
     for s in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
               "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_status_string",
-              "lcdm_launch_count"):
+              "lcdm_launch_count", "lcdm_between_workspace_size", "lcdm_distances_between", "lcdm_limits"):
         assert s in syms
 
 
@@ -54,6 +54,37 @@ def test_host_argument_checks(cdll):
     st = cdll.lcdm_distances(None, ctypes.c_int64(1), None, None, ctypes.c_int64(0), out, None,
                              ctypes.byref(good), None, ctypes.c_size_t(0), None)
     assert st == 1
+
+
+def test_general_limits_argument_checks(cdll):
+    from paper_2212_01937_gb300.lcdm import Opts
+    n = ctypes.c_size_t()
+    csr, shared = Opts(4, 1, 0, 0, 0), Opts(4, 1, 2, 0, 0)
+    i64 = ctypes.c_int64
+    assert cdll.lcdm_between_workspace_size(i64(16), i64(100), ctypes.byref(csr), ctypes.byref(n)) == 0
+    small = n.value
+    assert cdll.lcdm_between_workspace_size(i64(16), i64(200), ctypes.byref(csr), ctypes.byref(n)) == 0
+    assert n.value > small
+    # the shared layout has no per-row z1 shift; n = 0 (lcdm_limits) accepts any layout
+    assert cdll.lcdm_between_workspace_size(i64(16), i64(100), ctypes.byref(shared), ctypes.byref(n)) == 1
+    assert cdll.lcdm_between_workspace_size(i64(16), i64(0), ctypes.byref(shared), ctypes.byref(n)) == 0
+    out = (ctypes.c_void_p * 6)()
+    vp = ctypes.c_void_p
+    # z1 missing -> invalid, before any CUDA call
+    st = cdll.lcdm_distances_between(vp(8), i64(1), None, vp(8), vp(8), i64(4), None, out, None, vp(8),
+                                     ctypes.byref(csr), None, ctypes.c_size_t(0), None)
+    assert st == 1
+    # gradient without cotangents -> invalid
+    st = cdll.lcdm_distances_between(vp(8), i64(1), vp(8), vp(8), vp(8), i64(4), None, out, vp(8), vp(8),
+                                     ctypes.byref(csr), None, ctypes.c_size_t(0), None)
+    assert st == 1
+    # limits: nothing requested -> invalid; missing workspace -> workspace error
+    st = cdll.lcdm_limits(vp(8), i64(1), vp(8), None, None, None, None, None, vp(8), ctypes.byref(csr),
+                          None, ctypes.c_size_t(0), None)
+    assert st == 1
+    st = cdll.lcdm_limits(vp(8), i64(1), vp(8), vp(8), None, None, None, None, vp(8), ctypes.byref(csr),
+                          None, ctypes.c_size_t(0), None)
+    assert st == 3
 
 
 def test_python_binding_fails_loudly_without_library(monkeypatch, tmp_path):
