@@ -318,6 +318,7 @@ struct BetweenCarve {
     double* params4;
     double* jac;
     double* scale;
+    float4* rowf;
     double* gradp;
     char* zp;
     char* cotp[LCDM_NOUT];
@@ -334,6 +335,7 @@ BetweenCarve between_carve(char* base, int64_t B, int64_t npairs, int ncol, size
     c.params4 = (double*)take((size_t)B * 4 * sizeof(double));
     c.jac = (double*)take((size_t)B * 4 * ncol * sizeof(double));
     c.scale = (double*)take((size_t)B * sizeof(double));
+    c.rowf = (float4*)take((size_t)B * sizeof(float4));
     c.gradp = (double*)take((size_t)B * 4 * sizeof(double));
     c.zp = take((size_t)npairs * es);
     for (int i = 0; i < LCDM_NOUT; i++) c.cotp[i] = nullptr;
@@ -362,6 +364,7 @@ lcdm_status between_setup(const double* params, int64_t B, const double* z1, int
     sa.params4 = w.params4;
     sa.jac = w.jac;
     sa.scale = w.scale;
+    sa.rowf = w.rowf;
     if (launch_shift(sa, stream) != cudaSuccess) return LCDM_ERR_CUDA;
     g_launches++;
     return run_prep(w.params4, B, opts4, w.rec, status, gradp, nullptr, stream);
@@ -406,6 +409,7 @@ lcdm_status lcdm_distances_between(const double* params, int64_t B, const double
     m.fp64 = opts->precision == LCDM_FP64;
     m.z1 = z1;
     m.scale = w.scale;
+    m.rowf = w.rowf;
     m.z2 = z2;
     m.zp = w.zp;
     const void* cotk[LCDM_NOUT] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};

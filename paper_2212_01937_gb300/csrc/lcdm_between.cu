@@ -27,6 +27,7 @@ __global__ void shift_kernel(ShiftArgs a) {
         for (int i = 0; i < 4; i++) q[i] = nan;
         for (int i = 0; i < 4 * nc; i++) J[i] = nan;
         a.scale[b] = nan;
+        a.rowf[b] = make_float4(nan, nan, nan, nan);
         return;
     }
     const double iE = 1.0 / E1, rE = sqrt(E1);
@@ -48,6 +49,10 @@ __global__ void shift_kernel(ShiftArgs a) {
         for (int i = 0; i < 3; i++) J[(1 + i) * nc + c] = (pw[i] * d[i] - q[1 + i] * dE) * iE;
     }
     a.scale[b] = s;
+    // z1 as an unevaluated float sum hi + lo, so that z2 - z1 and the sign test
+    // z2 >= z1 come out right in float32 arithmetic when z2 is close to z1
+    const float hi = (float)z1;
+    a.rowf[b] = make_float4(hi, (float)(z1 - (double)hi), (float)(1.0 / s), (float)s);
 }
 
 cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s) {
@@ -57,47 +62,101 @@ cudaError_t launch_shift(const ShiftArgs& a, cudaStream_t s) {
 }
 
 // ------------------------------------------------------- per-pair maps -----
-__device__ __forceinline__ int64_t pair_row(const PairMapArgs& a, int64_t p) {
-    if (!a.offsets) return p / a.nrow;
-    int64_t lo = 0, hi = a.B;   // offsets[lo] <= p < offsets[hi]
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (__ldg(a.offsets + mid) <= p) lo = mid; else hi = mid;
+// Each warp takes a contiguous run of pairs, lane l every 32nd pair from l
+// (coalesced); the row of a lane's first pair comes from a binary search of
+// the CSR offsets, later rows from stepping forward.
+struct RowWalk {
+    const int64_t* off;
+    int64_t B, nrow, row;
+    __device__ int64_t at(int64_t p) {
+        if (!off) {
+            if (row < 0) row = p / nrow;
+            while ((row + 1) * nrow <= p) row++;
+            return row;
+        }
+        if (row < 0) {
+            int64_t lo = 0, hi = B;   // off[lo] <= p < off[hi]
+            while (hi - lo > 1) {
+                int64_t mid = (lo + hi) >> 1;
+                if (__ldg(off + mid) <= p) lo = mid; else hi = mid;
+            }
+            row = lo;
+        }
+        while (row < B - 1 && __ldg(off + row + 1) <= p) row++;
+        return row;
     }
-    return lo;
+};
+
+#define LCDM_MAP_BLOCK 256
+#define LCDM_MAP_BLOCKS_PER_SM 8
+
+__device__ __forceinline__ void warp_run(int64_t nnz, int64_t& p0, int64_t& p1) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x / 32);
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    int64_t chunk = (nnz + nw - 1) / nw;
+    chunk = (chunk + 31) / 32 * 32;
+    p0 = min(nnz, w * chunk);
+    p1 = min(nnz, p0 + chunk);
 }
 
-template <class T> __global__ void pair_pre_kernel(PairMapArgs a) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.nnz;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = pair_row(a, p);
-        const double z1 = a.z1[b], s = a.scale[b];
-        const double z2 = (double)reinterpret_cast<const T*>(a.z2)[p];
+// z' = (z2 - z1) / s, the domain test z2 >= z1, and the output / cotangent
+// factors (s for d_C and d_M, s^3 for d_abs, 1 otherwise), in the pass type
+template <class T> struct RowMap;
+template <> struct RowMap<float> {
+    float hi, lo, is, s;
+    __device__ RowMap(const PairMapArgs& a, int64_t b) {
+        const float4 r = a.rowf[b];
+        hi = r.x; lo = r.y; is = r.z; s = r.w;
+    }
+    // (z2 - hi) is exact near z1 (Sterbenz) and its sign is exact; lo is
+    // |z1 - hi| rounded, which keeps the sign of the tie z2 == hi
+    __device__ float dz(float z2) const { return (z2 - hi) - lo; }
+    __device__ float zp(float d) const { return d * is; }
+    __device__ float f(int o) const { return o == 2 ? s * s * s : ((o == 0 || o == 3) ? s : 1.0f); }
+};
+template <> struct RowMap<double> {
+    double z1, s;
+    __device__ RowMap(const PairMapArgs& a, int64_t b) : z1(a.z1[b]), s(a.scale[b]) {}
+    __device__ double dz(double z2) const { return z2 - z1; }
+    __device__ double zp(double d) const { return d / s; }
+    __device__ double f(int o) const { return o == 2 ? s * s * s : ((o == 0 || o == 3) ? s : 1.0); }
+};
+
+template <class T> __global__ void __launch_bounds__(LCDM_MAP_BLOCK) pair_pre_kernel(PairMapArgs a) {
+    int64_t p0, p1;
+    warp_run(a.nnz, p0, p1);
+    RowWalk rw{a.offsets, a.B, a.nrow, -1};
+    for (int64_t p = p0 + (threadIdx.x & 31); p < p1; p += 32) {
+        const RowMap<T> m(a, rw.at(p));
+        const T d = m.dz(reinterpret_cast<const T*>(a.z2)[p]);
         // an interval with z2 < z1 is outside the domain: evaluated at z' = 0,
         // its outputs are set to NaN afterwards and it adds nothing to the gradient
-        const bool ok = z2 >= z1;
-        reinterpret_cast<T*>(a.zp)[p] = ok ? (T)((z2 - z1) / s) : (T)0;
-        const double f[6] = {s, 1.0, s * s * s, s, 1.0, 1.0};
+        const bool ok = d >= (T)0;
+        reinterpret_cast<T*>(a.zp)[p] = ok ? m.zp(d) : (T)0;
+#pragma unroll
         for (int o = 0; o < 6; o++)
             if (a.cotp[o]) {
                 const T g = reinterpret_cast<const T*>(a.cot[o])[p];
-                reinterpret_cast<T*>(a.cotp[o])[p] = ok ? (T)(f[o] * (double)g) : (T)0;
+                reinterpret_cast<T*>(a.cotp[o])[p] = ok ? m.f(o) * g : (T)0;
             }
     }
 }
 
-template <class T> __global__ void pair_post_kernel(PairMapArgs a) {
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < a.nnz;
-         p += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t b = pair_row(a, p);
-        const double z1 = a.z1[b], s = a.scale[b];
-        const double z2 = (double)reinterpret_cast<const T*>(a.z2)[p];
-        const bool ok = z2 >= z1;
-        const double f[6] = {s, 1.0, s * s * s, s, 1.0, 1.0};
+template <class T> __global__ void __launch_bounds__(LCDM_MAP_BLOCK) pair_post_kernel(PairMapArgs a) {
+    int64_t p0, p1;
+    warp_run(a.nnz, p0, p1);
+    RowWalk rw{a.offsets, a.B, a.nrow, -1};
+    for (int64_t p = p0 + (threadIdx.x & 31); p < p1; p += 32) {
+        const RowMap<T> m(a, rw.at(p));
+        const bool ok = m.dz(reinterpret_cast<const T*>(a.z2)[p]) >= (T)0;
+        // t, d_L and mu need no factor: they are touched only to mark a pair
+        // outside the domain
+#pragma unroll
         for (int o = 0; o < 6; o++)
             if (a.out[o]) {
                 T* v = reinterpret_cast<T*>(a.out[o]) + p;
-                *v = ok ? (f[o] == 1.0 ? *v : (T)(f[o] * (double)*v)) : (T)CUDART_NAN;
+                if (!ok) *v = (T)CUDART_NAN;
+                else if (o == 0 || o == 2 || o == 3) *v = m.f(o) * *v;
             }
     }
 }
@@ -106,21 +165,21 @@ static unsigned map_grid(int64_t nnz) {
     int dev = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    int64_t need = (nnz + 255) / 256, cap = (int64_t)sms * 8;
+    const int64_t need = (nnz + LCDM_MAP_BLOCK - 1) / LCDM_MAP_BLOCK, cap = (int64_t)sms * LCDM_MAP_BLOCKS_PER_SM;
     return (unsigned)(need < cap ? (need > 0 ? need : 1) : cap);
 }
 
 cudaError_t launch_pair_pre(const PairMapArgs& a, cudaStream_t s) {
     if (a.nnz <= 0) return cudaSuccess;
-    if (a.fp64) pair_pre_kernel<double><<<map_grid(a.nnz), 256, 0, s>>>(a);
-    else pair_pre_kernel<float><<<map_grid(a.nnz), 256, 0, s>>>(a);
+    if (a.fp64) pair_pre_kernel<double><<<map_grid(a.nnz), LCDM_MAP_BLOCK, 0, s>>>(a);
+    else pair_pre_kernel<float><<<map_grid(a.nnz), LCDM_MAP_BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_pair_post(const PairMapArgs& a, cudaStream_t s) {
     if (a.nnz <= 0) return cudaSuccess;
-    if (a.fp64) pair_post_kernel<double><<<map_grid(a.nnz), 256, 0, s>>>(a);
-    else pair_post_kernel<float><<<map_grid(a.nnz), 256, 0, s>>>(a);
+    if (a.fp64) pair_post_kernel<double><<<map_grid(a.nnz), LCDM_MAP_BLOCK, 0, s>>>(a);
+    else pair_post_kernel<float><<<map_grid(a.nnz), LCDM_MAP_BLOCK, 0, s>>>(a);
     return cudaGetLastError();
 }
 

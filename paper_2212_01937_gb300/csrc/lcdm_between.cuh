@@ -36,6 +36,7 @@ struct ShiftArgs {
     double* params4;        // [B][4] (H0', Om', OL', Or'), closure
     double* jac;            // [B][4][ncol] d params4 / d params
     double* scale;          // [B] s = 1 + z1 (NaN for an invalid row)
+    float4* rowf;           // [B] (z1 hi, z1 lo, 1/s, s) in float32 for the FP32 pair maps
 };
 
 struct PairMapArgs {
@@ -46,6 +47,7 @@ struct PairMapArgs {
     int fp64;               // z, outputs and cotangents are float64 (else float32)
     const double* z1;       // [B]
     const double* scale;    // [B]
+    const float4* rowf;     // [B] float32 row constants (FP32 maps)
     const void* z2;         // [nnz]
     void* zp;               // [nnz] z' = (z2 - z1) / s
     const void* cot[6];     // user cotangents
