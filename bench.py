@@ -144,6 +144,7 @@ def main():
     ap.add_argument("--no-ragged", action="store_true", help="skip the ragged log-likelihood step timing")
     ap.add_argument("--no-limits", action="store_true",
                     help="skip the general-limits and age/horizon timings")
+    ap.add_argument("--no-bhm", action="store_true", help="skip the latent-redshift VI step timing")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -273,6 +274,8 @@ def main():
         if not args.no_limits:
             line["between_step"] = between_step_rate(dev)
             line["limits_step"] = limits_rate(dev)
+        if not args.no_bhm:
+            line["bhm_step"] = bhm_step_rate(dev)
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -356,6 +359,32 @@ def ragged_step_rate(dev, steps=10):
     ms = graph_ms(lambda: lcdm.gauss_loglike(params, z, m, off, M=d.M, sigma=d.sigma, call=call), dev, reps=steps)
     return {"workload": d.name + " (16384 cosmologies x floor(10^U(0,5)) z, CSR), FP32, CUDA-graph replay",
             "pairs_per_step": int(d.nnz), "ms_per_step": ms, "value": d.nnz / (ms / 1e3), "unit": UNIT}
+
+
+def bhm_step_rate(dev, steps=10):
+    """One VI step of the Sec. 4 model with latent redshifts: 10^6 mock SNe,
+    4 guide samples (partial-MVN guide over (Om, OL) and every log-redshift),
+    fused magnitude log-likelihood with its gradients w.r.t. (Om, OL) and each
+    latent redshift, redshift likelihood and gamma prior, ELBO gradient, Adam;
+    replayed from its CUDA graph."""
+    import torch
+    from paper_2212_01937_gb300 import bhm, workloads
+    d = workloads.bhm_supernovae()
+    vi = bhm.PMVNGuideVI(torch.tensor(d.extra["z_hat"], device=dev), torch.tensor(d.m_obs, device=dev), samples=4)
+    for _ in range(3):
+        vi.step()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        vi.step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    return {"workload": d.name + " x 4 guide samples (latent redshifts, Gamma(2, rate 3) prior, sigma_mu 0.14, "
+                                 "sigma_z 0.04), FP32, CUDA-graph replay",
+            "ms_per_step": ms, "pairs_per_step": vi.pairs_per_step, "value": vi.pairs_per_step / (ms / 1e3),
+            "unit": UNIT}
 
 
 def between_step_rate(dev):

@@ -157,6 +157,23 @@ lcdm_status lcdm_gauss_loglike(const double* params, int64_t B, const int64_t* o
                                double* grad, void* mu_out, int32_t* cosmo_status, const lcdm_opts* opts,
                                void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* lcdm_gauss_loglike plus the derivative of each row's log-likelihood with
+ * respect to the redshift of each of its pairs, for models whose redshifts
+ * are parameters (the latent redshifts of the Sec. 4 supernova model):
+ *   grad_z[i] = (m_obs_i - mu_i - M) / sigma^2 * d mu_i / d z_i,
+ *   d mu / dz = (5 / ln 10) [ 1/(1+z) + S_k'(D) / (E(z) S_k(D)) ],
+ * from d chi / dz = (c/H0) / E(z), the integrand of eq. (2.3) at its upper
+ * limit, and the curvature map (D = chi H0 / c).
+ *   grad_z [npairs] in the pass dtype (required); pairs with z = 0 get 0 (mu is
+ *   -inf there); rows with a bad cosmo_status get NaN.
+ *   ws: lcdm_loglike_dz_workspace_size(B, n, opts) bytes, 256-byte aligned.
+ * Other arguments as lcdm_gauss_loglike.                                    */
+lcdm_status lcdm_loglike_dz_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts, size_t* bytes);
+lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                  const void* m_obs, int64_t n, double M, double sigma, double* loglike,
+                                  double* grad, void* grad_z, void* mu_out, int32_t* cosmo_status,
+                                  const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
+
 /* Device workspace, in bytes, of lcdm_distances_vjp_host for B cosmologies
  * and n pairs (records, parameters, offsets, status, gradient, and the z,
  * cotangent and output arrays of all six outputs). */

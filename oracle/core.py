@@ -5,6 +5,7 @@ import numpy as np
 from . import build as _build
 
 OUT_NAMES = ("d_C", "t", "X", "d_M", "d_L", "mu")
+C_KMS = 299792.458   # speed of light, km/s
 
 _lib = None
 
@@ -117,6 +118,25 @@ def carlson_distances(params, z, offsets=None, roots=None, perm=None, return_ima
         _dp(z), z.size, _dp(packed), nroot.ctypes.data_as(i32p), perm.ctypes.data_as(i32p),
         _dp(out), _dp(imag))
     return (out, imag) if return_imag else out
+
+
+def dmu_dz(params, z, offsets=None, rtol=1e-14):
+    """d mu / d z of O1.  The derivative of eq. (2.3) with respect to its upper
+    limit is the integrand there, (c/H0) / E(z), E from eq. (2.2); through the
+    curvature map d_M = (c/H0) S_k(D), D = chi H0 / c, and d_L = (1+z) d_M
+    (Sec. 2.1.1, fn22):  d mu/dz = (5/ln 10) [1/(1+z) + S_k'(D) / (E S_k(D))]."""
+    params, z, offsets, B, ncol = _csr(params, z, offsets)
+    o = quad_distances(params, z, offsets, rtol)
+    rows = np.repeat(np.arange(B), np.diff(offsets))
+    H0, Om, OL, Or = (params[rows, k] for k in range(4))
+    Ok = params[rows, 4] if ncol == 5 else 1.0 - Om - OL - Or
+    x = 1.0 + z
+    E = np.sqrt(Or * x ** 4 + Om * x ** 3 + Ok * x ** 2 + OL)
+    DH = C_KMS / H0
+    D, S = o[:, 0] / DH, o[:, 3] / DH
+    r = np.sqrt(np.abs(Ok))
+    SD = np.where(Ok > 0, np.cosh(r * D), np.where(Ok < 0, np.cos(r * D), 1.0))
+    return 5.0 / np.log(10.0) * (1.0 / x + SD / (E * S))
 
 
 def _z1(z1, B):

@@ -10,6 +10,7 @@
 #include "lcdm_between.cuh"
 #include "lcdm_launch.cuh"
 #include "lcdm_prep.cuh"
+#include "lcdm_redshift.cuh"
 
 using namespace lcdm;
 
@@ -435,6 +436,61 @@ lcdm_status lcdm_distances_between(const double* params, int64_t B, const double
         if (launch_chain(w.jac, w.gradp, B, ncol, grad, stream) != cudaSuccess) return LCDM_ERR_CUDA;
         g_launches++;
     }
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_loglike_dz_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts, size_t* bytes) {
+    if (!opts_ok(opts) || B <= 0 || n < 0 || !bytes) return LCDM_ERR_INVALID;
+    const int64_t npairs = opts->layout == LCDM_LAYOUT_CSR ? n : B * n;
+    const size_t es = opts->precision == LCDM_FP64 ? 8 : 4;
+    *bytes = align256(ws_bytes_for(B)) + 2 * align256((size_t)npairs * es);
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                  const void* m_obs, int64_t n, double M, double sigma, double* loglike,
+                                  double* grad, void* grad_z, void* mu_out, int32_t* cosmo_status,
+                                  const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!m_obs || !loglike || !grad_z || !(sigma > 0) || !std::isfinite(M)) return LCDM_ERR_INVALID;
+    lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
+    if (st != LCDM_OK) return st;
+    size_t need = 0;
+    lcdm_loglike_dz_workspace_size(B, n, opts, &need);
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return LCDM_ERR_WORKSPACE;
+    const int64_t npairs = opts->layout == LCDM_LAYOUT_CSR ? n : B * n;
+    const size_t es = opts->precision == LCDM_FP64 ? 8 : 4;
+    Carved cv;
+    carve(ws, ws_bytes, B, cv);
+    char* dC = (char*)ws + align256(ws_bytes_for(B));
+    char* mu = dC + align256((size_t)npairs * es);
+    if (mu_out) mu = (char*)mu_out;
+    void* out[LCDM_NOUT] = {dC, nullptr, nullptr, nullptr, nullptr, mu};
+    Plan P;
+    make_plan(params, B, offsets, z, n, out, nullptr, nullptr, m_obs, M, sigma, grad, loglike, cosmo_status, opts,
+              cv, P);
+    st = run_prep(params, B, opts, cv, cosmo_status, grad, loglike, stream);
+    if (st != LCDM_OK) return st;
+    st = launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
+    if (st != LCDM_OK) return st;
+    DzArgs d;
+    d.params = params;
+    d.ncol = opts->ncol;
+    d.status = cosmo_status;
+    d.offsets = offsets;
+    d.layout = opts->layout;
+    d.nrow = n;
+    d.nnz = npairs;
+    d.B = B;
+    d.fp64 = opts->precision == LCDM_FP64;
+    d.z = z;
+    d.mobs = m_obs;
+    d.dC = dC;
+    d.mu = mu;
+    d.M = M;
+    d.sigma = sigma;
+    d.grad_z = grad_z;
+    if (launch_loglike_dz(d, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+    g_launches++;
     return LCDM_OK;
 }
 

@@ -60,13 +60,16 @@ def load():
     lib.lcdm_between_workspace_size.argtypes = [i64, i64, op, ctypes.POINTER(sz)]
     lib.lcdm_distances_between.argtypes = [_vp, i64, _vp, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, op, _vp, sz, _vp]
     lib.lcdm_limits.argtypes = [_vp, i64, _vp, _vp, _vp, _vp, _vp, _vp, _vp, op, _vp, sz, _vp]
+    lib.lcdm_loglike_dz_workspace_size.argtypes = [i64, i64, op, ctypes.POINTER(sz)]
+    lib.lcdm_gauss_loglike_dz.argtypes = [_vp, i64, _vp, _vp, _vp, i64, dbl, dbl, _vp, _vp, _vp, _vp, _vp, op,
+                                          _vp, sz, _vp]
     lib.lcdm_status_string.argtypes = [ctypes.c_int]
     lib.lcdm_status_string.restype = ctypes.c_char_p
     lib.lcdm_launch_count.restype = i64
     for f in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
               "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_host_workspace_size",
               "lcdm_distances_vjp_host", "lcdm_between_workspace_size", "lcdm_distances_between",
-              "lcdm_limits"):
+              "lcdm_limits", "lcdm_loglike_dz_workspace_size", "lcdm_gauss_loglike_dz"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -298,14 +301,30 @@ class HostVJP:
 
 
 def gauss_loglike(params, z, m_obs, offsets=None, M=-19.3, sigma=0.1, grad=True, want_mu=False,
-                  call=None, **kw):
+                  call=None, grad_z=False, workspace=None, **kw):
     """Gaussian log-likelihood of magnitudes per cosmology and its gradient
-    (lcdm_gauss_loglike).  Returns {"loglike": [B], "grad": [B, ncol], ...}."""
+    (lcdm_gauss_loglike).  Returns {"loglike": [B], "grad": [B, ncol], ...};
+    with grad_z, also "grad_z" [npairs], the derivative of each row's
+    log-likelihood with respect to each pair's redshift
+    (lcdm_gauss_loglike_dz; ``workspace``: a reusable uint8 device buffer of
+    lcdm_loglike_dz_workspace_size bytes)."""
     c = call if call is not None else Call(params, z, offsets, **kw)
     m = m_obs.to(device=c.device, dtype=c.dtype).contiguous()
     ll = torch.empty(c.B, dtype=torch.float64, device=c.device)
     g = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device) if grad else None
     mu = torch.empty(c.npairs, dtype=c.dtype, device=c.device) if want_mu else None
+    if grad_z:
+        gz = torch.empty(c.npairs, dtype=c.dtype, device=c.device)
+        ws = workspace if workspace is not None else loglike_dz_workspace(c)
+        _check(load().lcdm_gauss_loglike_dz(*c.common()[:4], _ptr(m), c.n, float(M), float(sigma), _ptr(ll), _ptr(g),
+                                            _ptr(gz), _ptr(mu), _ptr(c.status), ctypes.byref(c.opts), _ptr(ws),
+                                            ws.numel(), _stream(c.device)))
+        res = {"loglike": ll, "status": c.status, "grad_z": gz}
+        if grad:
+            res["grad"] = g
+        if want_mu:
+            res["mu"] = mu
+        return res
     _check(load().lcdm_gauss_loglike(*c.common()[:4], _ptr(m), c.n, float(M), float(sigma), _ptr(ll), _ptr(g),
                                      _ptr(mu), _ptr(c.status), *c.tail()))
     res = {"loglike": ll, "status": c.status}
@@ -314,6 +333,13 @@ def gauss_loglike(params, z, m_obs, offsets=None, M=-19.3, sigma=0.1, grad=True,
     if want_mu:
         res["mu"] = mu
     return res
+
+
+def loglike_dz_workspace(c):
+    """Device workspace of lcdm_gauss_loglike_dz for a prepared Call."""
+    nbytes = ctypes.c_size_t()
+    _check(load().lcdm_loglike_dz_workspace_size(c.B, c.n, ctypes.byref(c.opts), ctypes.byref(nbytes)))
+    return torch.empty(nbytes.value, dtype=torch.uint8, device=c.device)
 
 
 def autotune(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), cot=None, **kw):

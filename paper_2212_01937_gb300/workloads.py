@@ -221,3 +221,23 @@ def limits_batch(B=65536, seed=6):
         z1[b] = rng.uniform(0.0, 10.0) if b % 2 == 0 else 10.0 ** rng.uniform(1.0, np.log10(1100.0))
     return Batch("limits-%d" % B, params, np.zeros(0), np.zeros(B + 1, dtype=np.int64),
                  extra={"z1": z1})
+
+
+def bhm_supernovae(N=1_000_000, seed=7, truth=(0.3, 0.7), H0=70.0, alpha=2.0, beta=3.0, sigma_mu=0.14,
+                   sigma_z=0.04, mu=None):
+    """Mock data of the Sec. 4 supernova model: latent z ~ Gamma(alpha, rate
+    beta), observed zhat ~ N(z, (1+z)^2 sigma_z^2), observed distance modulus
+    muhat ~ N(mu(z), sigma_mu^2) for a radiationless cosmology (Om, OL) =
+    truth.  ``mu`` maps latent redshifts to distance moduli; by default the
+    cosmographic series mock_mu (tests pass exact distances).  The stand-in
+    for the paper's mock sets of 10^3 to 10^6 SNe."""
+    rng = np.random.default_rng(seed)
+    z = rng.gamma(alpha, 1.0 / beta, N)
+    z = np.maximum(z, 1e-4)
+    zhat = z + (1.0 + z) * sigma_z * rng.normal(size=N)
+    m = mock_mu(z, H0, truth[0], truth[1], 0.0) if mu is None else mu(z)
+    muhat = m + sigma_mu * rng.normal(size=N)
+    params = np.array([[H0, truth[0], truth[1], 0.0]])
+    return Batch("bhm-sn-%d" % N, params, z, np.array([0, N], dtype=np.int64), m_obs=muhat, M=0.0,
+                 sigma=sigma_mu, extra={"z_hat": zhat, "alpha": alpha, "beta": beta, "sigma_z": sigma_z,
+                                        "truth": truth, "H0": H0})

@@ -30,7 +30,8 @@ def test_header_declares_entry_points():
     syms = declared_symbols()
     for s in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
               "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_status_string",
-              "lcdm_launch_count", "lcdm_between_workspace_size", "lcdm_distances_between", "lcdm_limits"):
+              "lcdm_launch_count", "lcdm_between_workspace_size", "lcdm_distances_between", "lcdm_limits",
+              "lcdm_loglike_dz_workspace_size", "lcdm_gauss_loglike_dz"):
         assert s in syms
 
 

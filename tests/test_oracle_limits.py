@@ -184,3 +184,21 @@ def test_empty_and_reversed_intervals():
     assert np.all(np.isnan(o[1]))
     o2 = oracle.carlson_between(p, [1.0], np.array([1.0, 0.5]))
     assert np.all(o2[0, :5] == 0.0) and np.all(np.isnan(o2[1]))
+
+
+def test_dmu_dz_closed_forms_and_differences():
+    """d mu / dz (the integrand of eq. 2.3 through the curvature map):
+    Milne (5/ln10)(1/z + 1/(2+z)); Einstein-de Sitter from its closed form;
+    central differences of the quadrature for curved cosmologies."""
+    z = np.array([0.01, 0.3, 1.0, 2.5, 6.0])
+    k = 5 / np.log(10)
+    g = oracle.dmu_dz([H0, 0.0, 0.0, 0.0, 1.0], z)
+    assert rel(g, k * (1 / z + 1 / (2 + z))) < 1e-12
+    x = 1 + z
+    g = oracle.dmu_dz([H0, 1.0, 0.0, 0.0, 0.0], z)
+    dm = 2 * (1 - x ** -0.5)
+    assert rel(g, k * (1 / x + x ** -1.5 / dm)) < 1e-12
+    for p in ([70.0, 0.3, 0.7, 5e-5], [65.0, 0.2, 0.3, 8e-5], [75.0, 0.5, 1.1, 1e-5]):
+        h = 1e-5 * z
+        fd = (oracle.quad_distances(p, z + h)[:, 5] - oracle.quad_distances(p, z - h)[:, 5]) / (2 * h)
+        assert rel(oracle.dmu_dz(p, z), fd) < 1e-8
