@@ -20,6 +20,9 @@ std::atomic<int64_t> g_launches{0};
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// largest batch whose root preparation uses four lanes per cosmology
+#define LCDM_PREP_GROUP_MAX_B 16384
+
 size_t ws_bytes_for(int64_t B) {
     return align256((size_t)B * NREC * sizeof(double)) + align256((size_t)B * NREC * sizeof(float2));
 }
@@ -168,10 +171,21 @@ lcdm_status launch_plan(Plan& P, int block, int bps, int lane_map, cudaStream_t 
 
 lcdm_status run_prep(const double* params, int64_t B, const lcdm_opts* opts, const Carved& cv, int32_t* status,
                      double* grad, double* loglike, cudaStream_t s) {
-    // one warp per block: the FP64 work spreads over as many SMs as possible
-    int block = 32;
-    int64_t grid = (B + block - 1) / block;
-    prep_kernel<<<(unsigned)grid, block, 0, s>>>(params, B, opts->ncol, cv.recD, cv.recF, status, grad, loglike);
+    // One warp per block, so that the FP64 work spreads over as many SMs as
+    // possible.  Up to LCDM_PREP_GROUP_MAX_B cosmologies the solve is bound by
+    // the latency of one cosmology's dependent FP64 chain and four lanes share
+    // each root solve; beyond that the FP64 pipe is the bound and one lane per
+    // cosmology does no repeated work.
+    const int block = 32;
+    if (B <= LCDM_PREP_GROUP_MAX_B) {
+        const int64_t grid = (4 * B + block - 1) / block;
+        prep_kernel<4><<<(unsigned)grid, block, 0, s>>>(params, B, opts->ncol, cv.recD, cv.recF, status, grad,
+                                                       loglike);
+    } else {
+        const int64_t grid = (B + block - 1) / block;
+        prep_kernel<1><<<(unsigned)grid, block, 0, s>>>(params, B, opts->ncol, cv.recD, cv.recF, status, grad,
+                                                       loglike);
+    }
     g_launches++;
     return cudaGetLastError() == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
 }

@@ -76,10 +76,10 @@ LCDM_HD float fsin(float x) {
 #endif
 }
 
-// Roots of the monic polynomial c (degree n <= 4) by the Aberth-Ehrlich
-// iteration started on circles whose radii come from the Newton polygon of
-// log|c_k| (so a root near -Om/Or and the O(1) roots both start close).
-LCDM_HD int poly_roots(const double* c, int n, cd* z) {
+// Starting points of the root iteration for the monic polynomial c (degree
+// n <= 4): circles whose radii come from the Newton polygon of log|c_k|, so
+// that a root near -Om/Or and the O(1) roots both start close.
+LCDM_HD void start_points(const double* c, int n, cd* z) {
     // upper convex hull of (k, log|c_k|); single precision is enough for the start
     float lg[5];
     int idx[5], m = 0;
@@ -97,28 +97,62 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
     for (int e = 0; e + 1 < m; e++) {
         int a = idx[e], b = idx[e + 1], w = b - a;
         float rad = fexp((lg[a] - lg[b]) / w);
-        for (int j = 0; j < w; j++) {
+        for (int j = 0; j < w && r < 4; j++) {
             float ang = 6.2831853f * j / w + 6.2831853f * a / n + 0.4f;
             z[r++] = cmk(rad * fcos(ang), rad * fsin(ang));
         }
     }
-    for (; r < n; r++) z[r] = cmk(0.5 * r + 0.1, 0.3);  // (zero constant term etc.)
-    // single-precision iterations to about 1e-6 relative (short latency chains),
-    // then double precision from there (cubic convergence: two or three steps)
+    for (; r < 4; r++) z[r] = cmk(0.5 * r + 0.1, 0.3);  // (zero constant term etc.)
+}
+
+// Roots of the monic polynomial c (degree n <= 4) by the simultaneous
+// Aberth-Ehrlich iteration, G lanes per polynomial (G = 1 or 4): lane s of a
+// group of G consecutive lanes owns roots s, s + G, ... and reads the others'
+// current values by shuffles.  Four lanes cut the dependent chain of one
+// cosmology (few cosmologies: latency-bound); one lane does no repeated work
+// (many cosmologies: bound by the FP64 pipe).  Every lane of the warp must
+// call this (groups with active == false take part in the shuffles without
+// updating).  Single precision first, to about 1e-6 relative (short latency
+// chains), then double precision from there (cubic convergence: two or three
+// sweeps), stopping after a sweep with every correction below 1e-15 relative
+// or once the corrections stop shrinking (rounding level of a near-multiple
+// root); one Newton step per root at the end.  On return every lane of the
+// group holds all n roots in z.
+template <int G> __device__ void group_roots(const double* c, int n, bool active, cd* z) {
+    constexpr int R = 4 / G;   // roots per lane
+    const unsigned full = 0xffffffffu;
+    const int s = threadIdx.x & (G - 1);
+    cd z0[4];
+    start_points(c, n, z0);
+    double zre[R], zim[R];
+#pragma unroll
+    for (int r = 0; r < R; r++) { zre[r] = z0[r * G + s].re; zim[r] = z0[r * G + s].im; }
     {
-        float cf[5], zr[4], zi[4];
-        for (int k = 0; k <= n; k++) cf[k] = (float)c[k];
-        for (int i = 0; i < n; i++) { zr[i] = (float)z[i].re; zi[i] = (float)z[i].im; }
+        float cf[5];
+        for (int k = 0; k <= 4; k++) cf[k] = k <= n ? (float)c[k] : 0.f;
+        float zr[R], zi[R];
+#pragma unroll
+        for (int r = 0; r < R; r++) { zr[r] = (float)zre[r]; zi[r] = (float)zim[r]; }
+        bool done = !active;
 #pragma unroll 1
         for (int itf = 0; itf < 100; itf++) {
-            bool small = true;
-#pragma unroll 1
-            for (int i = 0; i < n; i++) {
+            float ar[4], ai[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                ar[k] = G == 1 ? zr[k / G] : __shfl_sync(full, zr[k / G], k % G, G);
+                ai[k] = G == 1 ? zi[k / G] : __shfl_sync(full, zi[k / G], k % G, G);
+            }
+            int small = 1;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int j = r * G + s;
+                if (done || j >= n) continue;
+                const float xr0 = ar[j], xi0 = ai[j];
                 float pr = cf[n], pi = 0.f, dr = 0.f, di = 0.f;
 #pragma unroll 1
                 for (int k = n - 1; k >= 0; k--) {
-                    float ndr = dr * zr[i] - di * zi[i] + pr, ndi = dr * zi[i] + di * zr[i] + pi;
-                    float npr = pr * zr[i] - pi * zi[i] + cf[k], npi = pr * zi[i] + pi * zr[i];
+                    float ndr = dr * xr0 - di * xi0 + pr, ndi = dr * xi0 + di * xr0 + pi;
+                    float npr = pr * xr0 - pi * xi0 + cf[k], npi = pr * xi0 + pi * xr0;
                     dr = ndr; di = ndi; pr = npr; pi = npi;
                 }
                 float dn = dr * dr + di * di;
@@ -126,67 +160,94 @@ LCDM_HD int poly_roots(const double* c, int n, cd* z) {
                 float idn = 1.0f / dn;
                 float rr = (pr * dr + pi * di) * idn, ri = (pi * dr - pr * di) * idn;   // p / p'
                 float sr = 0.f, si = 0.f;
-#pragma unroll 1
-                for (int j = 0; j < n; j++) {
-                    if (j == i) continue;
-                    float ar = zr[i] - zr[j], ai = zi[i] - zi[j], an2 = ar * ar + ai * ai;
-                    if (!(an2 > 0.f)) continue;
-                    float ia = 1.0f / an2;
-                    sr += ar * ia; si -= ai * ia;
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (k == j || k >= n) continue;
+                    float xr = xr0 - ar[k], xi = xi0 - ai[k], x2 = xr * xr + xi * xi;
+                    if (!(x2 > 0.f)) continue;
+                    float ix = 1.0f / x2;
+                    sr += xr * ix; si -= xi * ix;
                 }
                 float qr = 1.f - (rr * sr - ri * si), qi = -(rr * si + ri * sr);
                 float qn = qr * qr + qi * qi;
                 if (!(qn > 0.f)) continue;
                 float iq = 1.0f / qn;
                 float wr = (rr * qr + ri * qi) * iq, wi = (ri * qr - rr * qi) * iq;
-                zr[i] -= wr; zi[i] -= wi;
-                if (!(wr * wr + wi * wi < 1e-12f * (zr[i] * zr[i] + zi[i] * zi[i]) + 1e-30f)) small = false;
+                zr[r] = xr0 - wr; zi[r] = xi0 - wi;
+                if (!(wr * wr + wi * wi < 1e-12f * (zr[r] * zr[r] + zi[r] * zi[r]) + 1e-30f)) small = 0;
             }
-            if (small) break;
+            if (G > 1) {
+                small &= __shfl_xor_sync(full, small, 1, G);
+                small &= __shfl_xor_sync(full, small, 2, G);
+            }
+            if (small) done = true;
+            if (__all_sync(full, done)) break;
         }
-        for (int i = 0; i < n; i++)
-            if (isfinite(zr[i]) && isfinite(zi[i])) z[i] = cmk(zr[i], zi[i]);
+#pragma unroll
+        for (int r = 0; r < R; r++)
+            if (isfinite(zr[r]) && isfinite(zi[r])) { zre[r] = zr[r]; zim[r] = zi[r]; }
     }
-    // stop after two sweeps with every correction below 1e-15 relative, or once
-    // the corrections stop shrinking (rounding level of a near-multiple root)
-    int it = 0, settled = 0;
-    double prev = 1e300;
+    {
+        int settled = 0;
+        double prev = 1e300;
+        bool done = !active;
 #pragma unroll 1
-    for (; it < 200; it++) {
-        double worst = 0.0;
+        for (int it = 0; it < 200; it++) {
+            double br[4], bi[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                br[k] = G == 1 ? zre[k / G] : __shfl_sync(full, zre[k / G], k % G, G);
+                bi[k] = G == 1 ? zim[k / G] : __shfl_sync(full, zim[k / G], k % G, G);
+            }
+            double worst = 0.0;
+#pragma unroll
+            for (int r = 0; r < R; r++) {
+                const int j = r * G + s;
+                if (done || j >= n) continue;
+                cd zj = cmk(br[j], bi[j]), p, dp;
+                horner(c, n, zj, p, dp);
+                if (p.re == 0 && p.im == 0) continue;
+                cd ratio = cmul(p, crcp(dp));
+                cd sm = cmk(0, 0);
 #pragma unroll 1
-        for (int i = 0; i < n; i++) {
-            cd p, dp;
-            horner(c, n, z[i], p, dp);
-            if (p.re == 0 && p.im == 0) continue;
-            cd ratio = cmul(p, crcp(dp));
-            cd s = cmk(0, 0);
-#pragma unroll 1
-            for (int j = 0; j < n; j++)
-                if (j != i) s = cadd(s, crcp(csub(z[i], z[j])));
-            cd w = cmul(ratio, crcp(csub(cmk(1, 0), cmul(ratio, s))));
-            z[i] = csub(z[i], w);
-            const double rel = cnorm(w) * ddiv(1.0, cnorm(z[i]) + 1e-300);
-            if (!(rel <= worst)) worst = rel;
+                for (int k = 0; k < n; k++)
+                    if (k != j) sm = cadd(sm, crcp(csub(zj, cmk(br[k], bi[k]))));
+                cd w = cmul(ratio, crcp(csub(cmk(1, 0), cmul(ratio, sm))));
+                zj = csub(zj, w);
+                zre[r] = zj.re; zim[r] = zj.im;
+                const double rel = cnorm(w) * ddiv(1.0, cnorm(zj) + 1e-300);
+                if (!(rel <= worst)) worst = rel;   // a NaN counts as the worst
+            }
+            if (G > 1) {
+#pragma unroll
+                for (int o = 1; o < G; o <<= 1) {
+                    double v = __shfl_xor_sync(full, worst, o, G);
+                    if (!(v <= worst)) worst = v;
+                }
+            }
+            if (!done) {
+                if (worst < 1e-30) { if (++settled >= 1) done = true; }
+                else if (it >= 4 && worst >= 0.25 * prev) done = true;
+                prev = worst;
+            }
+            if (__all_sync(full, done)) break;
         }
-        if (worst < 1e-30) { if (++settled >= 1) break; }
-        else if (it >= 4 && worst >= 0.25 * prev) break;
-        prev = worst;
     }
     // Newton polishing
-    #pragma unroll 1
-    for (int i = 0; i < n; i++) {
-        #pragma unroll 1
-        for (int k = 0; k < 1; k++) {
-            cd p, dp;
-            horner(c, n, z[i], p, dp);
-            if (dp.re == 0 && dp.im == 0) break;
-            cd zn = csub(z[i], cmul(p, crcp(dp))), pn, dpn;
-            horner(c, n, zn, pn, dpn);
-            if (cnorm(pn) <= cnorm(p)) z[i] = zn; else break;
-        }
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        if (!active || r * G + s >= n) continue;
+        cd zj = cmk(zre[r], zim[r]), p, dp;
+        horner(c, n, zj, p, dp);
+        if (dp.re == 0 && dp.im == 0) continue;
+        cd zn = csub(zj, cmul(p, crcp(dp))), pn, dpn;
+        horner(c, n, zn, pn, dpn);
+        if (cnorm(pn) <= cnorm(p)) { zre[r] = zn.re; zim[r] = zn.im; }
     }
-    return it;
+#pragma unroll
+    for (int k = 0; k < 4; k++)
+        z[k] = G == 1 ? cmk(zre[k / G], zim[k / G])
+                      : cmk(__shfl_sync(full, zre[k / G], k % G, G), __shfl_sync(full, zim[k / G], k % G, G));
 }
 
 LCDM_HD void polish_real(const double* c, int n, double& x) {
@@ -202,8 +263,9 @@ LCDM_HD void polish_real(const double* c, int n, double& x) {
 }
 
 // Record of one cosmology from its parameter row p[ncol] = (H0, Om, OL, Or[, Ok]);
-// returns the status code.
-LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
+// returns the status code.  Called by the G lanes of a group together (see
+// group_roots); `active` is false for lanes past the last cosmology.
+template <int G> __device__ int prep_one(const double* p, int ncol, double* rec, bool active) {
     double H0 = p[0], Om = p[1], OL = p[2], Or = p[3];
     double Ok = ncol >= 5 ? p[4] : 1.0 - Om - OL - Or;
     for (int i = 0; i < NREC; i++) rec[i] = 0;
@@ -215,12 +277,15 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
     cd z[4];
     double alpha[5] = {OL, 0.0, Ok, Om, Or};
     double an = alpha[n];
-    double c[5];
+    double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    c[n] = 1.0;
     if (st == ST_OK) {
         const double ian = ddiv(1.0, an);
         for (int k = 0; k <= n; k++) c[k] = alpha[k] * ian;
         c[n] = 1.0;
-        poly_roots(c, n, z);
+    }
+    group_roots<G>(c, n, active && st == ST_OK, z);   // every lane, outside any divergent branch
+    if (st == ST_OK) {
         // classification: real when the imaginary part is negligible
         int nreal = 0, ir[4], ic[4], ncx = 0;
         #pragma unroll 1
@@ -394,23 +459,31 @@ LCDM_HD int prep_one(const double* p, int ncol, double* rec) {
     return st;
 }
 
-// One thread per cosmology.  grad / loglike (optional): rows initialised to 0
-// (NaN for a bad status).
+// G lanes per cosmology (see group_roots); grad / loglike (optional): rows
+// initialised to 0 (NaN for a bad status).  Launched with 32-thread blocks
+// over G B threads.
+template <int G>
 __global__ void prep_kernel(const double* __restrict__ params, int64_t B, int ncol, double* __restrict__ recD,
                             float2* __restrict__ recF, int32_t* __restrict__ status, double* __restrict__ grad,
                             double* __restrict__ loglike) {
-    int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= B) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t b = t / G;
+    const int j = (int)(t % G);
+    const bool inb = b < B;
+    // lanes past the end work on a copy of the last row and write nothing
+    const double* prow = params + (inb ? b : B - 1) * ncol;
     double rec[NREC];
-    int st = prep_one(params + b * ncol, ncol, rec);
+    const int st = prep_one<G>(prow, ncol, rec, inb);
+    if (!inb) return;
     double* rd = recD + b * NREC;
     float2* rf = recF + b * NREC;
     #pragma unroll 1
-    for (int i = 0; i < NREC; i++) {
+    for (int i = j; i < NREC; i += G) {
         rd[i] = rec[i];
         float h = (float)rec[i];
         rf[i] = make_float2(h, (float)(rec[i] - (double)h));
     }
+    if (j != 0) return;
     status[b] = st;
     double init = st == ST_OK ? 0.0 : nan("");
     if (grad)
