@@ -52,7 +52,9 @@
  *                Omega_m0 <= 0 when Omega_r0 == 0)
  *              3 degenerate roots (coincident roots or rho_A == 0)
  *              4 duplication did not converge / principal value not available
- *              5 root configuration not supported (two complex pairs)
+ *              5 root configuration not supported (two complex pairs, or
+ *                the triple root at z = -1 of Omega_L0 = Omega_k0 = 0:
+ *                Einstein-de Sitter, flat matter + radiation)
  *            and every output of such a cosmology is NaN.
  *   z = 0    gives d = t = X = 0, mu = -inf; tangents of mu with respect to
  *            the Omega columns are 0 and d mu / d H0 = -5 / (H0 ln 10).
