@@ -176,6 +176,20 @@ lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t
                                   double* grad, void* grad_z, void* mu_out, int32_t* cosmo_status,
                                   const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream);
 
+/* lcdm_distances_vjp plus the derivative with respect to each pair's
+ * redshift: grad_z[i] = sum_o cot[o][i] d out_o / dz_i, from the integrands
+ * of eqs. (2.3)-(2.5) at the upper limit, (c/H0)/E, 1/(H0 (1+z) E) and
+ * (c/H0)(1+z)^2/E, through the curvature map, d_L = (1+z) d_M and mu
+ * (d mu/dz counts as 0 at z = 0).  grad_z [npairs] in the pass dtype
+ * (required; for the shared layout one entry per (row, redshift) pair).
+ * grad may be NULL (then only grad_z and the forward outputs are computed).
+ *   ws: lcdm_loglike_dz_workspace_size(B, n, opts) bytes, 256-byte aligned.
+ * Other arguments as lcdm_distances_vjp.                                   */
+lcdm_status lcdm_distances_vjp_dz(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                  int64_t n, const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT],
+                                  double* grad, void* grad_z, int32_t* cosmo_status, const lcdm_opts* opts,
+                                  void* ws, size_t ws_bytes, cudaStream_t stream);
+
 /* Device workspace, in bytes, of lcdm_distances_vjp_host for B cosmologies
  * and n pairs (records, parameters, offsets, status, gradient, and the z,
  * cotangent and output arrays of all six outputs). */

@@ -18,12 +18,14 @@ Parity status: every function here is pinned by ``tests/test_oracle_*.py``
 """
 from .core import (carlson, quad_distances, carlson_distances, simpson,
                    set_mutation, OUT_NAMES, quad_between, quad_limits,
-                   carlson_between, carlson_limits, dmu_dz)
+                   carlson_between, carlson_limits, dmu_dz,
+                   dout_dz)
 from .roots import (poly_coeffs_x, roots_x, root_coef_jacobian,
                     root_param_jacobian, classify_roots, permutations)
 
 __all__ = ["carlson", "quad_distances", "carlson_distances", "simpson",
            "quad_between", "quad_limits", "carlson_between", "carlson_limits", "dmu_dz",
+           "dout_dz",
            "set_mutation", "OUT_NAMES", "poly_coeffs_x", "roots_x",
            "root_coef_jacobian", "root_param_jacobian", "classify_roots",
            "permutations"]

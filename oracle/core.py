@@ -120,11 +120,13 @@ def carlson_distances(params, z, offsets=None, roots=None, perm=None, return_ima
     return (out, imag) if return_imag else out
 
 
-def dmu_dz(params, z, offsets=None, rtol=1e-14):
-    """d mu / d z of O1.  The derivative of eq. (2.3) with respect to its upper
-    limit is the integrand there, (c/H0) / E(z), E from eq. (2.2); through the
-    curvature map d_M = (c/H0) S_k(D), D = chi H0 / c, and d_L = (1+z) d_M
-    (Sec. 2.1.1, fn22):  d mu/dz = (5/ln 10) [1/(1+z) + S_k'(D) / (E S_k(D))]."""
+def dout_dz(params, z, offsets=None, rtol=1e-14):
+    """Derivatives of O1's six outputs with respect to the redshift (the upper
+    limit).  The derivative of each integral (2.3)-(2.5) with respect to its
+    upper limit is its integrand there: (c/H0)/E, 1/(H0 (1+z) E),
+    (c/H0)(1+z)^2/E, E from eq. (2.2); then d_M = (c/H0) S_k(D), D = chi H0/c,
+    d_L = (1+z) d_M and mu (Sec. 2.1.1, fn22).  Returns [nnz, 6] in the order of
+    OUT_NAMES; d mu/dz is 0 at z = 0 (mu = -inf there)."""
     params, z, offsets, B, ncol = _csr(params, z, offsets)
     o = quad_distances(params, z, offsets, rtol)
     rows = np.repeat(np.arange(B), np.diff(offsets))
@@ -133,10 +135,25 @@ def dmu_dz(params, z, offsets=None, rtol=1e-14):
     x = 1.0 + z
     E = np.sqrt(Or * x ** 4 + Om * x ** 3 + Ok * x ** 2 + OL)
     DH = C_KMS / H0
+    tH = 977.7922216807891 / H0
     D, S = o[:, 0] / DH, o[:, 3] / DH
     r = np.sqrt(np.abs(Ok))
     SD = np.where(Ok > 0, np.cosh(r * D), np.where(Ok < 0, np.cos(r * D), 1.0))
-    return 5.0 / np.log(10.0) * (1.0 / x + SD / (E * S))
+    d = np.zeros((z.size, 6))
+    d[:, 0] = DH / E
+    d[:, 1] = tH / (x * E)
+    d[:, 2] = DH * x * x / E
+    d[:, 3] = DH * SD / E
+    d[:, 4] = o[:, 3] + x * d[:, 3]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        d[:, 5] = np.where(z > 0, 5.0 / np.log(10.0) * (1.0 / x + SD / (E * S)), 0.0)
+    return d
+
+
+def dmu_dz(params, z, offsets=None, rtol=1e-14):
+    """d mu / d z of O1 (the last column of dout_dz):
+    (5/ln 10) [1/(1+z) + S_k'(D) / (E S_k(D))]."""
+    return dout_dz(params, z, offsets, rtol)[:, 5]
 
 
 def _z1(z1, B):

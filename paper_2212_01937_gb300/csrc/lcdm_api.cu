@@ -502,6 +502,53 @@ lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t
     d.mu = mu;
     d.M = M;
     d.sigma = sigma;
+    for (int i = 0; i < LCDM_NOUT; i++) d.cot[i] = nullptr;
+    d.vjp = 0;
+    d.grad_z = grad_z;
+    if (launch_loglike_dz(d, stream) != cudaSuccess) return LCDM_ERR_CUDA;
+    g_launches++;
+    return LCDM_OK;
+}
+
+lcdm_status lcdm_distances_vjp_dz(const double* params, int64_t B, const int64_t* offsets, const void* z,
+                                  int64_t n, const void* const cot[LCDM_NOUT], void* const out[LCDM_NOUT],
+                                  double* grad, void* grad_z, int32_t* cosmo_status, const lcdm_opts* opts,
+                                  void* ws, size_t ws_bytes, cudaStream_t stream) {
+    if (!cot || !grad_z) return LCDM_ERR_INVALID;
+    lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
+    if (st != LCDM_OK) return st;
+    size_t need = 0;
+    lcdm_loglike_dz_workspace_size(B, n, opts, &need);
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return LCDM_ERR_WORKSPACE;
+    const int64_t npairs = opts->layout == LCDM_LAYOUT_CSR ? n : B * n;
+    Carved cv;
+    carve(ws, ws_bytes, B, cv);
+    void* outk[LCDM_NOUT];
+    for (int i = 0; i < LCDM_NOUT; i++) outk[i] = out ? out[i] : nullptr;
+    if (!outk[LCDM_DC]) outk[LCDM_DC] = (char*)ws + align256(ws_bytes_for(B));   // d_C feeds the z-derivatives
+    Plan P;
+    make_plan(params, B, offsets, z, n, outk, nullptr, grad ? cot : nullptr, nullptr, 0, 1, grad, nullptr,
+              cosmo_status, opts, cv, P);
+    st = run_prep(params, B, opts, cv, cosmo_status, grad, nullptr, stream);
+    if (st != LCDM_OK) return st;
+    st = launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
+    if (st != LCDM_OK) return st;
+    DzArgs d;
+    memset(&d, 0, sizeof(d));
+    d.params = params;
+    d.ncol = opts->ncol;
+    d.status = cosmo_status;
+    d.offsets = offsets;
+    d.layout = opts->layout;
+    d.nrow = n;
+    d.nnz = npairs;
+    d.B = B;
+    d.fp64 = opts->precision == LCDM_FP64;
+    d.z = z;
+    d.dC = outk[LCDM_DC];
+    d.sigma = 1.0;
+    for (int i = 0; i < LCDM_NOUT; i++) d.cot[i] = cot[i];
+    d.vjp = 1;
     d.grad_z = grad_z;
     if (launch_loglike_dz(d, stream) != cudaSuccess) return LCDM_ERR_CUDA;
     g_launches++;

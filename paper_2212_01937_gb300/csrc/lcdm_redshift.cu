@@ -1,5 +1,6 @@
-// Per-pair derivative of the Gaussian log-likelihood of magnitudes (Sec. 4)
-// with respect to the pair's redshift; see lcdm_redshift.cuh.
+// Per-pair derivatives with respect to the pair's redshift: of the Gaussian
+// log-likelihood of magnitudes (Sec. 4), or of a cotangent-weighted sum of
+// the outputs; see lcdm_redshift.cuh.
 #include <math_constants.h>
 
 #include "lcdm_kernels.cuh"
@@ -38,17 +39,29 @@ template <class T> __global__ void __launch_bounds__(256) loglike_dz_kernel(DzAr
         const T Om = (T)pr[1], OL = (T)pr[2], Or = (T)pr[3];
         const T Ok = a.ncol == 5 ? (T)pr[4] : (T)(1.0 - pr[1] - pr[2] - pr[3]);
         const T z = reinterpret_cast<const T*>(a.z)[zi];
-        if (z == (T)0) { *out = (T)0; continue; }   // mu = -inf there: no finite derivative
+        if (z == (T)0 && !a.vjp) { *out = (T)0; continue; }   // mu = -inf there: no finite derivative
         const T x = (T)1 + z, x2 = x * x;
         const T E = sqrt(((Or * x + Om) * x + Ok) * x2 + OL);          // eq. (2.2)
         const T DH = (T)(LCDM_C_KMS / pr[0]);
         const T D = reinterpret_cast<const T*>(a.dC)[p] / DH;
         T S, SD, Sk;
         curv_map<T>(D, Ok, S, SD, Sk);
-        const T dmu = c5 * ((T)1 / x + SD / (E * S));
-        const T mu = reinterpret_cast<const T*>(a.mu)[p];
-        const T r = reinterpret_cast<const T*>(a.mobs)[zi] - mu - (T)a.M;
-        *out = r * inv_s2 * dmu;
+        const T dmu = z == (T)0 ? (T)0 : c5 * ((T)1 / x + SD / (E * S));
+        if (!a.vjp) {
+            const T mu = reinterpret_cast<const T*>(a.mu)[p];
+            const T r = reinterpret_cast<const T*>(a.mobs)[zi] - mu - (T)a.M;
+            *out = r * inv_s2 * dmu;
+            continue;
+        }
+        // the integrands of eqs. (2.3)-(2.5) at the upper limit, then the observables
+        const T iE = (T)1 / E;
+        const T dM = DH * SD * iE;
+        const T d[6] = {DH * iE, (T)(LCDM_HUBBLE_GYR / pr[0]) * iE / x, DH * x2 * iE, dM, DH * S + x * dM, dmu};
+        T g = 0;
+#pragma unroll
+        for (int o = 0; o < 6; o++)
+            if (a.cot[o]) g += reinterpret_cast<const T*>(a.cot[o])[p] * d[o];
+        *out = g;
     }
 }
 

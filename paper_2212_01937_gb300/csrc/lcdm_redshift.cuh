@@ -23,11 +23,18 @@ struct DzArgs {
     const void* z;          // [n] (shared) or [nnz]
     const void* mobs;       // like z
     const void* dC;         // [nnz] comoving distance of each pair
-    const void* mu;         // [nnz] distance modulus of each pair
+    const void* mu;         // [nnz] distance modulus of each pair (likelihood mode)
     double M, sigma;
-    void* grad_z;           // [nnz] d loglike_row / d z_pair
+    const void* cot[6];     // VJP mode: cotangents of the six outputs (null = zero)
+    int vjp;                // 0: likelihood mode, 1: VJP mode
+    void* grad_z;           // [nnz] d loglike_row / d z_pair, or sum_o cot_o d out_o / dz
 };
 
+// Likelihood mode: grad_z = (m_obs - mu - M) / sigma^2 * d mu/dz.
+// VJP mode: grad_z = sum_o cot_o d out_o/dz with
+//   d chi/dz = (c/H0)/E, d t/dz = 1/(H0 (1+z) E), d d_abs/dz = (c/H0)(1+z)^2/E,
+//   d d_M/dz = (c/H0) S_k'(D)/E, d d_L/dz = d_M + (1+z) d d_M/dz, d mu/dz as above
+//   (0 at z = 0, where mu = -inf).
 cudaError_t launch_loglike_dz(const DzArgs& a, cudaStream_t s);
 
 }  // namespace lcdm

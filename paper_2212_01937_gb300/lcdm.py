@@ -63,13 +63,15 @@ def load():
     lib.lcdm_loglike_dz_workspace_size.argtypes = [i64, i64, op, ctypes.POINTER(sz)]
     lib.lcdm_gauss_loglike_dz.argtypes = [_vp, i64, _vp, _vp, _vp, i64, dbl, dbl, _vp, _vp, _vp, _vp, _vp, op,
                                           _vp, sz, _vp]
+    lib.lcdm_distances_vjp_dz.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, _vp, op, _vp, sz, _vp]
     lib.lcdm_status_string.argtypes = [ctypes.c_int]
     lib.lcdm_status_string.restype = ctypes.c_char_p
     lib.lcdm_launch_count.restype = i64
     for f in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
               "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_host_workspace_size",
               "lcdm_distances_vjp_host", "lcdm_between_workspace_size", "lcdm_distances_between",
-              "lcdm_limits", "lcdm_loglike_dz_workspace_size", "lcdm_gauss_loglike_dz"):
+              "lcdm_limits", "lcdm_loglike_dz_workspace_size", "lcdm_gauss_loglike_dz",
+              "lcdm_distances_vjp_dz"):
         getattr(lib, f).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -189,16 +191,25 @@ def distances_jac(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), jac_
     return out
 
 
-def distances_vjp(params, z, cot, offsets=None, outputs=(), call=None, **kw):
+def distances_vjp(params, z, cot, offsets=None, outputs=(), call=None, grad_z=False, workspace=None, **kw):
     """Fused forward + adjoint (lcdm_distances_vjp): grad [B, ncol] of
     sum_o <cot[o], out_o>.  cot: {name: tensor [npairs]}.  A prepared
-    ``call`` (same params, z, offsets) skips the argument set-up."""
+    ``call`` (same params, z, offsets) skips the argument set-up.  With
+    grad_z, also "grad_z" [npairs] = sum_o cot_o d out_o / dz per pair
+    (lcdm_distances_vjp_dz; ``workspace`` as for gauss_loglike)."""
     c = call if call is not None else Call(params, z, offsets, **kw)
     out, vp = c.out_buffers(outputs)
     cots = {n: v.to(device=c.device, dtype=c.dtype).contiguous() for n, v in cot.items() if v is not None}
     cp = _VP6(*[(cots[n].data_ptr() if n in cots else None) for n in OUTS])
     grad = torch.empty(c.B, c.ncol, dtype=torch.float64, device=c.device)
-    _check(load().lcdm_distances_vjp(*c.common(), cp, vp, _ptr(grad), _ptr(c.status), *c.tail()))
+    if grad_z:
+        gz = torch.empty(c.npairs, dtype=c.dtype, device=c.device)
+        ws = workspace if workspace is not None else loglike_dz_workspace(c)
+        _check(load().lcdm_distances_vjp_dz(*c.common(), cp, vp, _ptr(grad), _ptr(gz), _ptr(c.status),
+                                            ctypes.byref(c.opts), _ptr(ws), ws.numel(), _stream(c.device)))
+        out["grad_z"] = gz
+    else:
+        _check(load().lcdm_distances_vjp(*c.common(), cp, vp, _ptr(grad), _ptr(c.status), *c.tail()))
     out["grad"] = grad
     out["status"] = c.status
     return out
@@ -359,10 +370,12 @@ def autotune(params, z, offsets=None, outputs=("d_C", "t", "X", "mu"), cot=None,
 
 
 class Distances(torch.autograd.Function):
-    """d_C, t, X, d_M, d_L, mu as differentiable functions of params.
+    """d_C, t, X, d_M, d_L, mu as differentiable functions of params and of
+    the redshifts (csr and dense layouts).
 
     Forward runs lcdm_distances; backward runs the fused forward+adjoint
-    kernel (lcdm_distances_vjp) with the incoming gradients as cotangents."""
+    kernel (lcdm_distances_vjp, or lcdm_distances_vjp_dz when the redshifts
+    need a gradient) with the incoming gradients as cotangents."""
 
     @staticmethod
     def forward(ctx, params, z, offsets, outputs, layout, precision):
@@ -376,8 +389,13 @@ class Distances(torch.autograd.Function):
         params, z, offsets = ctx.saved_tensors
         outputs, layout, precision, has_off = ctx.meta
         cot = {n: g for n, g in zip(outputs, grads) if g is not None}
-        res = distances_vjp(params, z, cot, offsets if has_off else None, layout=layout, precision=precision)
-        return res["grad"].to(params.dtype), None, None, None, None, None
+        want_z = ctx.needs_input_grad[1]
+        if want_z and layout == "shared":
+            raise ValueError("redshift gradients need the csr or dense layout")
+        res = distances_vjp(params, z, cot, offsets if has_off else None, layout=layout, precision=precision,
+                            grad_z=want_z)
+        gz = res["grad_z"].reshape(z.shape).to(z.dtype) if want_z else None
+        return res["grad"].to(params.dtype), gz, None, None, None, None
 
 
 def distances_autograd(params, z, offsets=None, outputs=("d_C", "mu"), layout=None, precision="fp32"):

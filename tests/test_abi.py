@@ -31,7 +31,7 @@ def test_header_declares_entry_points():
     for s in ("lcdm_workspace_size", "lcdm_roots", "lcdm_distances", "lcdm_distances_jac",
               "lcdm_distances_vjp", "lcdm_gauss_loglike", "lcdm_autotune", "lcdm_status_string",
               "lcdm_launch_count", "lcdm_between_workspace_size", "lcdm_distances_between", "lcdm_limits",
-              "lcdm_loglike_dz_workspace_size", "lcdm_gauss_loglike_dz"):
+              "lcdm_loglike_dz_workspace_size", "lcdm_gauss_loglike_dz", "lcdm_distances_vjp_dz"):
         assert s in syms
 
 

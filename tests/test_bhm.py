@@ -116,3 +116,58 @@ def test_bhm_vi_recovers_cosmology(lib):
     zg = vi.redshifts().double().cpu().numpy()
     zt, zh = d.z, d.extra["z_hat"]
     assert np.sqrt(np.mean((zg - zt) ** 2)) < np.sqrt(np.mean((zh - zt) ** 2))
+
+
+OUTS = ("d_C", "t", "X", "d_M", "d_L", "mu")
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_distances_grad_z_vs_oracle(lib, prec):
+    """lcdm_distances_vjp_dz: sum_o cot_o d out_o/dz per pair against the
+    oracle's integrands (eqs. 2.3-2.5 at the upper limit) through the
+    curvature map; z = 0 included (d mu/dz counts as 0 there).  The parameter
+    gradient is that of lcdm_distances_vjp."""
+    b = workloads.general_batch(B=5, n=64, seed=17, zmax=5.0)
+    dt = np.float64 if prec == "fp64" else np.float32
+    z = b.z.astype(dt)
+    z[::23] = 0.0
+    z[5::29] = 1100.0
+    zq = z.astype(np.float64)
+    rng = np.random.default_rng(7)
+    cot = {n: rng.normal(size=z.size).astype(dt) for n in OUTS}
+    d = oracle.dout_dz(b.params, zq, b.offsets)
+    want = sum(cot[n].astype(np.float64) * d[:, k] for k, n in enumerate(OUTS))
+    res = lib.distances_vjp(_t(b.params), _t(z), {n: _t(v) for n, v in cot.items()}, _t(b.offsets),
+                            grad_z=True, precision=prec)
+    plain = lib.distances_vjp(_t(b.params), _t(z), {n: _t(v) for n, v in cot.items()}, _t(b.offsets),
+                              precision=prec)
+    torch.cuda.synchronize()
+    assert int(res["status"].abs().sum()) == 0
+    assert torch.equal(res["grad"], plain["grad"])
+    ref = oracle.quad_distances(b.params, zq, b.offsets)
+    cond = mu_cond(ref, b.params, b.offsets)
+    rel = 1e-10 if prec == "fp64" else 2e-5
+    bound = rel * cond * sum(np.abs(cot[n].astype(np.float64) * d[:, k]) for k, n in enumerate(OUTS))
+    got = res["grad_z"].double().cpu().numpy()
+    assert np.all(np.abs(got - want) <= bound + 1e-300), (prec, np.max(np.abs(got - want) / bound))
+
+
+def test_autograd_redshift_gradient(lib):
+    """torch.autograd through lcdm.Distances with redshifts that require a
+    gradient (FP64): z.grad against the oracle's z-derivatives."""
+    b = workloads.general_batch(B=4, n=50, seed=19)
+    params = _t(b.params).requires_grad_(True)
+    z = _t(b.z).requires_grad_(True)
+    off = _t(b.offsets)
+    rng = np.random.default_rng(9)
+    w = {n: rng.normal(size=b.nnz) for n in ("d_C", "t", "mu")}
+    d_C, t, mu = lib.distances_autograd(params, z, off, outputs=("d_C", "t", "mu"), precision="fp64")
+    loss = sum((_t(w[n]) * v).sum() for n, v in zip(("d_C", "t", "mu"), (d_C, t, mu)))
+    loss.backward()
+    torch.cuda.synchronize()
+    d = oracle.dout_dz(b.params, b.z, b.offsets)
+    want = w["d_C"] * d[:, 0] + w["t"] * d[:, 1] + w["mu"] * d[:, 5]
+    scale = np.abs(w["d_C"] * d[:, 0]) + np.abs(w["t"] * d[:, 1]) + np.abs(w["mu"] * d[:, 5])
+    got = z.grad.cpu().numpy()
+    assert np.all(np.abs(got - want) <= 1e-10 * scale), np.max(np.abs(got - want) / scale)
+    assert params.grad is not None and torch.isfinite(params.grad).all()

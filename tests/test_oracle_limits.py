@@ -202,3 +202,17 @@ def test_dmu_dz_closed_forms_and_differences():
         h = 1e-5 * z
         fd = (oracle.quad_distances(p, z + h)[:, 5] - oracle.quad_distances(p, z - h)[:, 5]) / (2 * h)
         assert rel(oracle.dmu_dz(p, z), fd) < 1e-8
+
+
+def test_dout_dz_against_differences():
+    """All six z-derivatives against central differences of the quadrature
+    (the integrands of eqs. 2.3-2.5 at the upper limit, the curvature map and
+    d_L = (1+z) d_M), for open, closed and flat cosmologies; and at z = 0 the
+    integrands at their lower end: d chi/dz = c/H0, d t/dz = 1/H0."""
+    z = np.array([0.01, 0.3, 1.0, 2.5, 6.0])
+    for p in ([70.0, 0.3, 0.7, 5e-5], [65.0, 0.2, 0.3, 8e-5], [75.0, 0.5, 1.1, 1e-5], [70.0, 0.3, 0.7, 0.0]):
+        h = 1e-5 * z
+        fd = (oracle.quad_distances(p, z + h) - oracle.quad_distances(p, z - h)) / (2 * h)[:, None]
+        assert rel(oracle.dout_dz(p, z), fd) < 1e-8, p
+    d0 = oracle.dout_dz([H0, 0.3, 0.7, 5e-5], [0.0])[0]
+    assert abs(d0[0] / DH - 1) < 1e-14 and abs(d0[1] / tH - 1) < 1e-14 and d0[5] == 0.0
