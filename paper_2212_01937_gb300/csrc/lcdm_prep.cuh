@@ -1,4 +1,4 @@
-// Root preparation, one thread per cosmology, FP64: factorise E^2 (eq. 3.2),
+// Root preparation, one or four lanes per cosmology, FP64: factorise E^2 (eq. 3.2),
 // classify the roots, choose the root labels, precompute the per-cosmology
 // constants and the root tangents (App. A, eqs. A.1-A.4).
 #pragma once
