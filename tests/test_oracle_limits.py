@@ -216,3 +216,29 @@ def test_dout_dz_against_differences():
         assert rel(oracle.dout_dz(p, z), fd) < 1e-8, p
     d0 = oracle.dout_dz([H0, 0.3, 0.7, 5e-5], [0.0])[0]
     assert abs(d0[0] / DH - 1) < 1e-14 and abs(d0[1] / tH - 1) < 1e-14 and d0[5] == 0.0
+
+
+def test_general_limits_and_age_mpmath():
+    """O1 with general limits and the age against mpmath quadrature at 30
+    digits (open and closed cosmologies with radiation; radiationless)."""
+    mp = __import__("pytest").importorskip("mpmath")
+    mp.mp.dps = 30
+    for p in ([70.0, 0.3, 0.7, 5e-5], [68.0, 0.45, 0.3, 8e-5], [72.0, 0.2, 1.0, 2e-5], [70.0, 0.3, 0.7, 0.0]):
+        Om, OL, Or = (mp.mpf(v) for v in p[1:4])
+        Ok = 1 - Om - OL - Or
+        Q = lambda a: Or + Om * a + Ok * a ** 2 + OL * a ** 4
+        DHm, tHm = mp.mpf(C) / p[0], mp.mpf(977.7922216807891) / p[0]
+        for z1, z2 in ((0.2, 0.25), (1.0, 4.0), (3.0, 1100.0)):
+            a1, a2 = 1 / (1 + mp.mpf(z1)), 1 / (1 + mp.mpf(z2))
+            ref = [DHm * mp.quad(lambda a: 1 / mp.sqrt(Q(a)), [a2, a1]),
+                   tHm * mp.quad(lambda a: a / mp.sqrt(Q(a)), [a2, a1]),
+                   DHm * mp.quad(lambda a: a ** -2 / mp.sqrt(Q(a)), [a2, a1])]
+            o = oracle.quad_between(p, [z1], np.array([z2]))[0]
+            assert rel(o[:3], np.array([float(v) for v in ref])) < 1e-13, (p, z1, z2)
+        for z1 in (0.0, 2.0, 50.0):
+            a1 = 1 / (1 + mp.mpf(z1))
+            # in s = sqrt(a): the integrands stay bounded at a = 0 for the radiationless case too
+            age = tHm * mp.quad(lambda s: 2 * s ** 3 / mp.sqrt(Q(s * s)), [0, mp.sqrt(a1)])
+            hor = DHm * mp.quad(lambda s: 2 * s / mp.sqrt(Q(s * s)), [0, mp.sqrt(a1)])
+            o = oracle.quad_limits(p, [z1])[0]
+            assert rel(o, np.array([float(hor), float(age)])) < 1e-13, (p, z1)
