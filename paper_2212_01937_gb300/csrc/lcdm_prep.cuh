@@ -373,12 +373,23 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
                 const double irA = ddiv(1.0, rA);
                 rec[RF_EPSA] = -irA;
                 rec[RF_RHOA] = rA;
+                // Tangents of m_A = lam rho_A = y from the scaled quartic
+                //   F(y) = y^4 + Om y^3 + Ok Or y^2 + OL Or^3 = Or^3 E^2(rho_A) = 0,
+                // dy = -(dF/dtheta) / (dF/dy), a ratio of O(1) terms: in the Or
+                // direction rho_A d lam and lam d rho_A are each O(Om/Or) and cancel.
+                // a_A = -lam (rho_A - 1) = -y + lam.
+                const double y = Or * rA;
+                const double iFy = ddiv(1.0, y * y * (4.0 * y + 3.0 * Om) + 2.0 * Ok * Or * y);
+                const double cl = ncol == 4 ? 1.0 : 0.0, FOk = Or * y * y;
+                const double Fth[4] = {y * y * y - cl * FOk, Or * Or * Or - cl * FOk,
+                                       Ok * y * y + 3.0 * OL * Or * Or - cl * FOk, FOk};
                 #pragma unroll 1
                 for (int k = 0; k < K; k++) {
                     double dl = (k == 2) ? 1.0 : 0.0, dA = dr[0][k].re;
+                    const double dy = -Fth[k] * iFy;
                     rec[RF_DLAM + k] = dl;
-                    rec[RF_DAA + k] = -(dl * (rA - 1.0) + Or * dA);
-                    rec[RF_DMA + k] = dl * rA + Or * dA;
+                    rec[RF_DAA + k] = dl - dy;
+                    rec[RF_DMA + k] = dy;
                     rec[RF_DEPSA + k] = dA * (irA * irA);
                     rec[RF_DRHOA + k] = dA;
                 }
