@@ -28,7 +28,7 @@ UNIT = "pairs/s"
 OUTPUTS = ("d_C", "t", "X", "mu")
 # Work of the dominant kernel per pair for this workload: FP32 floating-point
 # operations (FFMA counted as 2, FADD and FMUL as 1) executed per pair, from
-# the ncu capture summarised in profiles/pairs_kernel_fp32_vjp_4096x1024.md.
+# an ncu capture of this kernel on this workload (its summary is under profiles/).
 FLOP_PER_PAIR = 5501.0
 # DRAM bytes (read + write) per launch of that kernel from the same capture
 # (None once the kernel has changed since the counters were taken).
