@@ -108,6 +108,44 @@ def cpu_oracle_rate(b, budget_s, seed=0):
     return n / t, n
 
 
+def cpu_model():
+    """Host CPU model (lscpu's model name, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_carlson_rate(b, budget_s, seed=0):
+    """The Carlson oracle (O2, eqs. 3.7-3.9 / B.1-B.3 from the companion-matrix
+    roots; forward values only) pairs/s on one thread, on a random sample."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    def run(n):
+        idx = np.sort(rng.choice(b.nnz, n, replace=False))
+        rows = np.searchsorted(b.offsets, idx, side="right") - 1
+        z = b.z[idx].astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.carlson_distances(b.params[rows], z, np.arange(n + 1))
+        return time.perf_counter() - t0
+    n0 = min(2000, b.nnz)
+    t = run(n0)
+    n = int(min(max(n0, budget_s / max(t, 1e-9) * n0), 2_000_000, b.nnz))
+    t = run(n)
+    return n / t, n
+
+
 def _oracle_chunk(task):
     """Worker of cpu_oracle_rate_all: the oracle on one slice of pairs
     (params rows, redshifts); returns the seconds it took."""
@@ -162,7 +200,8 @@ def reference_arm(args):
             "data": "synthetic", "config": base_config(b),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
                              "sample": "%d random pairs of the workload per step over %d processes (adaptive "
-                                       "quadrature forward + Leibniz gradient)" % (nsample, procs)},
+                                       "quadrature forward + Leibniz gradient)" % (nsample, procs),
+                             "cpu_model": cpu_model()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -292,7 +331,12 @@ def main():
             cpu = {"value": r, "unit": UNIT, "cores": procs, "kind": "oracle",
                    "sample": "%d random pairs of the workload split over %d processes (spawned), adaptive "
                              "quadrature forward + Leibniz gradient" % (n, procs),
-                   "single_thread": {"value": r1, "cores": 1, "sample": "%d random pairs, 1 thread" % n1}}
+                   "single_thread": {"value": r1, "cores": 1, "sample": "%d random pairs, 1 thread" % n1},
+                   "cpu_model": cpu_model()}
+            rc, nc = cpu_carlson_rate(b, budget_s=3.0)
+            cpu["carlson_forward_single_thread"] = {
+                "value": rc, "unit": UNIT, "cores": 1,
+                "sample": "%d random pairs, Carlson oracle forward only (no gradient), 1 thread" % nc}
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
