@@ -268,22 +268,26 @@ static void gl_init(void) {
     gl_ready = 1;
 }
 
-#define NCOMP 15 /* 3 forward integrands + 3 weights x 4 parameter directions */
+#define NCOMP 18 /* 3 forward integrands + 3 weights x 5 coefficient functions */
 
-typedef struct { double Om, OL, Or, Ok; } cosmo_t;
+/* Density parameters; Os (w = -1/3, scaling as (1+z)^2 like curvature but
+ * outside the curvature map) and Ox (w = -2/3, scaling as (1+z)) are the
+ * other components the method allows (fn4); both 0 unless given. */
+typedef struct { double Om, OL, Or, Ok, Os, Ox; } cosmo_t;
 
 /* Integrand vector at scale factor a.
  * [0..2]: w(a)/sqrt(Q) for w = 1, a, a^-2.
- * [3 + 4*iw + ig]: -(1/2) w(a) g(a) Q^-3/2 for g = dQ/dOm = a, dQ/dOL = a^4,
- *                  dQ/dOr = 1, dQ/dOk = a^2 (Leibniz rule under the integral). */
+ * [3 + 5*iw + ig]: -(1/2) w(a) g(a) Q^-3/2 for g = dQ/dOm = a, dQ/dOL = a^4,
+ *                  dQ/dOr = 1, dQ/dOk = dQ/dOs = a^2, dQ/dOx = a^3 (Leibniz
+ *                  rule under the integral). */
 static void integrand(double a, const cosmo_t* c, double* out) {
-    double Q = c->Or + c->Om * a + c->Ok * a * a + c->OL * a * a * a * a;
+    double Q = c->Or + c->Om * a + (c->Ok + c->Os) * a * a + c->Ox * a * a * a + c->OL * a * a * a * a;
     double iq = 1.0 / sqrt(Q), iq3 = iq / Q;
     double w[3] = {1.0, a, 1.0 / (a * a)};
-    double g[4] = {a, a * a * a * a, 1.0, a * a};
+    double g[5] = {a, a * a * a * a, 1.0, a * a, a * a * a};
     for (int iw = 0; iw < 3; iw++) {
         out[iw] = w[iw] * iq;
-        for (int ig = 0; ig < 4; ig++) out[3 + 4 * iw + ig] = -0.5 * w[iw] * g[ig] * iq3;
+        for (int ig = 0; ig < 5; ig++) out[3 + 5 * iw + ig] = -0.5 * w[iw] * g[ig] * iq3;
     }
 }
 
@@ -316,10 +320,15 @@ static void gl_rule(const cosmo_t* c, int mode, double anchor, double lo, double
  * about rtol).  At most MAX_INTERVALS intervals are evaluated; the return
  * value is the number of accepted intervals, negative if the cap was hit. */
 #define MAX_INTERVALS 200000
-#define KMASK_ALL 0x7fff
-/* every component except the absorption distance and its derivatives (which
- * diverge as z2 -> infinity) */
-#define KMASK_NO_X (KMASK_ALL & ~((1 << 2) | (0xf << 11)))
+#define KMASK_ALL 0x3ffff
+/* the values and the four density directions of the standard components */
+#define KMASK_STD (0x7 | (0xf << 3) | (0xf << 8) | (0xf << 13))
+/* everything but the absorption distance and its derivatives (which diverge
+ * as z2 -> infinity) */
+#define KMASK_NO_X (KMASK_ALL & ~((1 << 2) | (0x1f << 13)))
+/* components that decide the subdivision: the extra components' directions
+ * only when they are parameters */
+static int kmask_for(int ncol) { return ncol >= 7 ? KMASK_ALL : KMASK_STD; }
 static int adapt(const cosmo_t* c, int mode, double anchor, double lo, double hi, double rtol, int kmask,
                  double* total) {
     double whole[NCOMP], wabs[NCOMP];
@@ -368,16 +377,18 @@ static int quad_breakpoints(const cosmo_t* c, double lo, double hi, double* bp) 
     double prev = 0, aprev = lo;
     for (int i = 0; i <= NG; i++) {
         double a = lo + (hi - lo) * i / NG;
-        double d = c->Om + 2.0 * c->Ok * a + 4.0 * c->OL * a * a * a;
+        double d = c->Om + 2.0 * (c->Ok + c->Os) * a + 3.0 * c->Ox * a * a + 4.0 * c->OL * a * a * a;
         if (i > 0 && ((prev < 0) != (d < 0))) {
             double x0 = aprev, x1 = a, d0 = prev;
             for (int it = 0; it < 200; it++) {
-                double xm = 0.5 * (x0 + x1), dm = c->Om + 2.0 * c->Ok * xm + 4.0 * c->OL * xm * xm * xm;
+                double xm = 0.5 * (x0 + x1);
+                double dm = c->Om + 2.0 * (c->Ok + c->Os) * xm + 3.0 * c->Ox * xm * xm + 4.0 * c->OL * xm * xm * xm;
                 if ((dm < 0) == (d0 < 0)) { x0 = xm; d0 = dm; } else x1 = xm;
             }
             double as = 0.5 * (x0 + x1);
-            double Q = c->Or + c->Om * as + c->Ok * as * as + c->OL * as * as * as * as;
-            double Q2 = 2.0 * c->Ok + 12.0 * c->OL * as * as;
+            double Q = c->Or + c->Om * as + (c->Ok + c->Os) * as * as + c->Ox * as * as * as
+                       + c->OL * as * as * as * as;
+            double Q2 = 2.0 * (c->Ok + c->Os) + 6.0 * c->Ox * as + 12.0 * c->OL * as * as;
             double wd = (Q > 0 && Q2 != 0) ? sqrt(Q / fabs(Q2)) : 0.0;
             bp[n++] = as;
             for (int k = 1; k <= 64 && wd > 0; k *= 4) { bp[n++] = as - k * wd; bp[n++] = as + k * wd; }
@@ -437,10 +448,15 @@ static void integrate_between(const cosmo_t* c, double z1, double z2, double rto
     }
 }
 
+/* params rows: (H0, Om, OL, Or) with the closure Ok = 1 - Om - OL - Or;
+ * (H0, Om, OL, Or, Ok); or (H0, Om, OL, Or, Ok, Os, Ox) with the two further
+ * components of fn4 (every density explicit). */
 static void unpack_params(const double* p, int ncol, double* H0, cosmo_t* c) {
     *H0 = p[0];
     c->Om = p[1]; c->OL = p[2]; c->Or = p[3];
     c->Ok = (ncol >= 5) ? p[4] : 1.0 - p[1] - p[2] - p[3];
+    c->Os = (ncol >= 7) ? p[5] : 0.0;
+    c->Ox = (ncol >= 7) ? p[6] : 0.0;
 }
 
 /* Row of pair j in a CSR batch (offsets == NULL: every row holds nnz/B). */
@@ -469,7 +485,7 @@ static void quad_pair(const cosmo_t* c, double H0, int ncol, double z1, double z
     if (z2 == z1) {
         for (int k = 0; k < NCOMP; k++) Iv[k] = 0.0;
     } else {
-        integrate_between(c, z1, z2, rtol, KMASK_ALL, Iv);
+        integrate_between(c, z1, z2, rtol, kmask_for(ncol), Iv);
     }
     double S, SD, Sk;
     curv_map(Iv[0], c->Ok, &S, &SD, &Sk);
@@ -484,12 +500,13 @@ static void quad_pair(const cosmo_t* c, double H0, int ncol, double z1, double z
     J[5 * ncol + 0] = -5.0 / (log(10.0) * H0);
     /* Omega directions: dI_w/dtheta = sum_g (dQ/dtheta)_g-coefficients x J_w[g]. */
     for (int ip = 1; ip < ncol; ip++) {
-        /* coefficients of (a, a^4, 1, a^2) in dQ/dtheta, and dOk/dtheta */
-        double cg[4] = {0, 0, 0, 0}, dOk = 0;
+        /* coefficients of (a, a^4, 1, a^2, a^3) in dQ/dtheta, and dOk/dtheta */
+        double cg[5] = {0, 0, 0, 0, 0}, dOk = 0;
         if (ip == 1) cg[0] = 1;
         if (ip == 2) cg[1] = 1;
         if (ip == 3) cg[2] = 1;
-        if (ip == 4) cg[3] = 1;
+        if (ip == 4 || ip == 5) cg[3] = 1;   /* Ok and Os enter Q alike */
+        if (ip == 6) cg[4] = 1;
         if (ncol == 4) { /* closure: Ok = 1 - Om - OL - Or */
             if (!(g_mutation == 5 && ip == 1)) cg[3] = -1;
             dOk = -1;
@@ -499,7 +516,7 @@ static void quad_pair(const cosmo_t* c, double H0, int ncol, double z1, double z
         double dI[3];
         for (int iw = 0; iw < 3; iw++) {
             dI[iw] = 0;
-            for (int ig = 0; ig < 4; ig++) dI[iw] += cg[ig] * Iv[3 + 4 * iw + ig];
+            for (int ig = 0; ig < 5; ig++) dI[iw] += cg[ig] * Iv[3 + 5 * iw + ig];
         }
         double ddM = DH * (SD * dI[0] + Sk * dOk);
         J[0 * ncol + ip] = DH * dI[0];
@@ -562,7 +579,7 @@ int oracle_quad_limits(const double* params, int64_t B, int ncol, const double* 
         cosmo_t c;
         unpack_params(params + b * ncol, ncol, &H0, &c);
         double DH = C_KMS / H0, tH = HUBBLE_TIME_GYR / H0, Iv[NCOMP];
-        integrate_between(&c, z1[b], INFINITY, rtol, KMASK_NO_X, Iv);
+        integrate_between(&c, z1[b], INFINITY, rtol, KMASK_NO_X & kmask_for(ncol), Iv);
         out[2 * b] = DH * Iv[0];
         out[2 * b + 1] = tH * Iv[1];
         if (!jac) continue;
@@ -570,11 +587,11 @@ int oracle_quad_limits(const double* params, int64_t B, int ncol, const double* 
         J[0] = -out[2 * b] / H0;
         J[ncol] = -out[2 * b + 1] / H0;
         for (int ip = 1; ip < ncol; ip++) {
-            double cg[4] = {0, 0, 0, 0};
-            cg[ip - 1] = 1;
+            double cg[5] = {0, 0, 0, 0, 0};
+            cg[ip <= 4 ? ip - 1 : (ip == 5 ? 3 : 4)] = 1;
             if (ncol == 4) cg[3] = -1;
             double d0 = 0, d1 = 0;
-            for (int ig = 0; ig < 4; ig++) { d0 += cg[ig] * Iv[3 + ig]; d1 += cg[ig] * Iv[7 + ig]; }
+            for (int ig = 0; ig < 5; ig++) { d0 += cg[ig] * Iv[3 + ig]; d1 += cg[ig] * Iv[8 + ig]; }
             J[ip] = DH * d0;
             J[ncol + ip] = tH * d1;
         }

@@ -14,12 +14,16 @@ import numpy as np
 
 def poly_coeffs_x(params):
     """Coefficients of E^2 in x = 1+z, lowest power first (eq. 2.2):
-    [OL, 0, Ok, Om, Or].  params rows (H0, Om, OL, Or[, Ok]); closure
-    Ok = 1 - Om - OL - Or when only four columns are given (Sec. 2.1)."""
+    [OL, Ox, Ok + Os, Om, Or].  params rows (H0, Om, OL, Or[, Ok[, Os, Ox]]);
+    closure Ok = 1 - Om - OL - Or when only four columns are given (Sec. 2.1);
+    Os (w = -1/3) and Ox (w = -2/3) are the further components of fn4, zero
+    unless given."""
     p = np.atleast_2d(np.asarray(params, dtype=np.float64))
     Om, OL, Or = p[:, 1], p[:, 2], p[:, 3]
     Ok = p[:, 4] if p.shape[1] >= 5 else 1.0 - Om - OL - Or
-    return np.stack([OL, np.zeros_like(OL), Ok, Om, Or], axis=1)
+    Os = p[:, 5] if p.shape[1] >= 7 else np.zeros_like(OL)
+    Ox = p[:, 6] if p.shape[1] >= 7 else np.zeros_like(OL)
+    return np.stack([OL, Ox, Ok + Os, Om, Or], axis=1)
 
 
 def _polish(coef_low, x, iters=4):
