@@ -21,6 +21,15 @@
  *            Omega_L0, Omega_r0) with Omega_k0 = 1 - Om - OL - Or (closure,
  *            Sec. 2.1) when ncol == 4, or a fifth column Omega_k0 (ncol == 5).
  *            Omega_r0 == 0 selects the cubic formulas of App. B.1.
+ *            ncol == 7 adds, after an explicit Omega_k0, the two further
+ *            components that keep E^2 a quartic (fn4): Omega_s0 (w = -1/3,
+ *            scaling as (1+z)^2 like curvature but outside the curvature map)
+ *            and Omega_x0 (w = -2/3, scaling as (1+z)); every density is then
+ *            explicit.  Seven-column rows carry no tangents: they are accepted
+ *            by lcdm_distances, lcdm_distances_static, lcdm_gauss_loglike
+ *            without grad, lcdm_roots without droots and lcdm_autotune
+ *            without grad; every entry point that needs tangents or the
+ *            per-row shift returns LCDM_ERR_UNSUPPORTED for them.
  *   pairs    layout LCDM_LAYOUT_CSR: offsets[B+1] int64 (offsets[0] = 0,
  *            non-decreasing, offsets[B] = n), z[n]; row b holds pairs
  *            offsets[b] .. offsets[b+1]-1.  Empty rows are allowed.
@@ -89,7 +98,7 @@ enum { LCDM_LAYOUT_CSR = 0, LCDM_LAYOUT_DENSE = 1, LCDM_LAYOUT_SHARED = 2 };
 enum { LCDM_DC = 0, LCDM_T = 1, LCDM_X = 2, LCDM_DM = 3, LCDM_DL = 4, LCDM_MU = 5, LCDM_NOUT = 6 };
 
 typedef struct {
-    int32_t ncol;           /* 4 (closure) or 5 (explicit Omega_k0)             */
+    int32_t ncol;           /* 4 (closure), 5 (explicit Omega_k0) or 7 (+ Os, Ox) */
     int32_t precision;      /* LCDM_FP64 or LCDM_FP32_MIXED                      */
     int32_t layout;         /* LCDM_LAYOUT_*                                     */
     int32_t block;          /* threads per block (multiple of 32, <= 256); 0 = tuned */

@@ -28,7 +28,8 @@ size_t ws_bytes_for(int64_t B) {
 }
 
 bool opts_ok(const lcdm_opts* o) {
-    return o && (o->ncol == 4 || o->ncol == 5) && (o->precision == LCDM_FP64 || o->precision == LCDM_FP32_MIXED) &&
+    return o && (o->ncol == 4 || o->ncol == 5 || o->ncol == 7) &&
+           (o->precision == LCDM_FP64 || o->precision == LCDM_FP32_MIXED) &&
            o->layout >= LCDM_LAYOUT_CSR && o->layout <= LCDM_LAYOUT_SHARED && o->block >= 0 && o->block <= 256 &&
            (o->block % 32) == 0 && o->blocks_per_sm >= 0 && o->blocks_per_sm <= 64 && o->lane_map >= LCDM_MAP_TUNED &&
            o->lane_map <= LCDM_MAP_INTERLEAVED;
@@ -130,6 +131,8 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
     a.sigma = sigma;
     a.grad = grad;
     a.loglike = loglike;
+    // rows with the further components (7 columns) have no tangent slots
+    if (tangents && opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;
     P.prec = opts->precision == LCDM_FP64 ? 0 : 1;
     P.K = tangents ? opts->ncol - 1 : 0;
     P.wt = wt;
@@ -227,7 +230,8 @@ lcdm_status pairs_common(const double* params, int64_t B, const int64_t* offsets
     st = carve(ws, ws_bytes, B, cv);
     if (st != LCDM_OK) return st;
     Plan P;
-    make_plan(params, B, offsets, z, n, out, jac, cot, mobs, M, sigma, grad, loglike, status, opts, cv, P);
+    st = make_plan(params, B, offsets, z, n, out, jac, cot, mobs, M, sigma, grad, loglike, status, opts, cv, P);
+    if (st != LCDM_OK) return st;
     st = run_prep(params, B, opts, cv, status, grad, loglike, stream);
     if (st != LCDM_OK) return st;
     return launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
@@ -404,6 +408,7 @@ lcdm_status lcdm_distances_between(const double* params, int64_t B, const double
     int64_t npairs = 0;
     if (between_npairs(B, n, opts, &npairs) != LCDM_OK || !z1 || (!out && !grad) || (grad && !cot))
         return LCDM_ERR_INVALID;
+    if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // the row shift takes 4 or 5 columns
     lcdm_status st = check_pairs_args(params, B, offsets, z2, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
     const int ncol = opts->ncol;
@@ -468,6 +473,7 @@ lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t
     if (!m_obs || !loglike || !grad_z || !(sigma > 0) || !std::isfinite(M)) return LCDM_ERR_INVALID;
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
+    if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // E(z) of the redshift kernel: 4 or 5 columns
     size_t need = 0;
     lcdm_loglike_dz_workspace_size(B, n, opts, &need);
     if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return LCDM_ERR_WORKSPACE;
@@ -480,8 +486,9 @@ lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t
     if (mu_out) mu = (char*)mu_out;
     void* out[LCDM_NOUT] = {dC, nullptr, nullptr, nullptr, nullptr, mu};
     Plan P;
-    make_plan(params, B, offsets, z, n, out, nullptr, nullptr, m_obs, M, sigma, grad, loglike, cosmo_status, opts,
-              cv, P);
+    st = make_plan(params, B, offsets, z, n, out, nullptr, nullptr, m_obs, M, sigma, grad, loglike, cosmo_status,
+                   opts, cv, P);
+    if (st != LCDM_OK) return st;
     st = run_prep(params, B, opts, cv, cosmo_status, grad, loglike, stream);
     if (st != LCDM_OK) return st;
     st = launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
@@ -517,6 +524,7 @@ lcdm_status lcdm_distances_vjp_dz(const double* params, int64_t B, const int64_t
     if (!cot || !grad_z) return LCDM_ERR_INVALID;
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
+    if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // E(z) of the redshift kernel: 4 or 5 columns
     size_t need = 0;
     lcdm_loglike_dz_workspace_size(B, n, opts, &need);
     if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return LCDM_ERR_WORKSPACE;
@@ -527,8 +535,9 @@ lcdm_status lcdm_distances_vjp_dz(const double* params, int64_t B, const int64_t
     for (int i = 0; i < LCDM_NOUT; i++) outk[i] = out ? out[i] : nullptr;
     if (!outk[LCDM_DC]) outk[LCDM_DC] = (char*)ws + align256(ws_bytes_for(B));   // d_C feeds the z-derivatives
     Plan P;
-    make_plan(params, B, offsets, z, n, outk, nullptr, grad ? cot : nullptr, nullptr, 0, 1, grad, nullptr,
-              cosmo_status, opts, cv, P);
+    st = make_plan(params, B, offsets, z, n, outk, nullptr, grad ? cot : nullptr, nullptr, 0, 1, grad, nullptr,
+                   cosmo_status, opts, cv, P);
+    if (st != LCDM_OK) return st;
     st = run_prep(params, B, opts, cv, cosmo_status, grad, nullptr, stream);
     if (st != LCDM_OK) return st;
     st = launch_plan(P, opts->block, opts->blocks_per_sm, opts->lane_map, stream);
@@ -560,6 +569,7 @@ lcdm_status lcdm_limits(const double* params, int64_t B, const double* z1, doubl
                         const lcdm_opts* opts, void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (!opts_ok(opts) || B <= 0 || !params || !z1 || !cosmo_status || (!chi_inf && !t_inf && !grad))
         return LCDM_ERR_INVALID;
+    if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // the row shift takes 4 or 5 columns
     const int ncol = opts->ncol;
     if (!ws || ((uintptr_t)ws & 255) != 0) return LCDM_ERR_WORKSPACE;
     BetweenCarve w = between_carve((char*)ws, B, 0, ncol, 8);
@@ -617,6 +627,7 @@ lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64
         (n > 0 && !z) || !cot || !grad || !cosmo_status || nchunks < 1 || nchunks > LCDM_HOST_MAX_CHUNKS)
         return LCDM_ERR_INVALID;
     if (offsets[0] != 0 || offsets[B] != n) return LCDM_ERR_INVALID;
+    if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // no tangent slots for 7-column rows
     for (int64_t r = 0; r < B; r++)
         if (offsets[r + 1] < offsets[r]) return LCDM_ERR_INVALID;
     const int ncol = opts->ncol;
@@ -703,6 +714,7 @@ lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes)
 lcdm_status lcdm_roots(const double* params, int64_t B, const lcdm_opts* opts, double* roots, double* droots,
                        int32_t* kind, int32_t* cosmo_status, void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (!opts_ok(opts) || !params || !cosmo_status || B <= 0) return LCDM_ERR_INVALID;
+    if (droots && opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // no tangent slots for 7-column rows
     Carved cv;
     lcdm_status st = carve(ws, ws_bytes, B, cv);
     if (st != LCDM_OK) return st;
@@ -760,7 +772,9 @@ lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offset
     st = carve(ws, ws_bytes, B, cv);
     if (st != LCDM_OK) return st;
     Plan P;
-    make_plan(params, B, offsets, z, n, out, nullptr, cot, nullptr, 0, 1, grad, nullptr, cosmo_status, opts, cv, P);
+    st = make_plan(params, B, offsets, z, n, out, nullptr, cot, nullptr, 0, 1, grad, nullptr, cosmo_status, opts, cv,
+                   P);
+    if (st != LCDM_OK) return st;
     const PairsTable& t = table(P.prec, P.K);
     int idx = (P.wt ? 2 : 0) + (P.wx ? 1 : 0);
     cudaEvent_t e0, e1;

@@ -268,14 +268,19 @@ LCDM_HD void polish_real(const double* c, int n, double& x) {
 template <int G> __device__ int prep_one(const double* p, int ncol, double* rec, bool active) {
     double H0 = p[0], Om = p[1], OL = p[2], Or = p[3];
     double Ok = ncol >= 5 ? p[4] : 1.0 - Om - OL - Or;
+    // the further components of fn4 (7-column rows): Os (w = -1/3) scales as
+    // (1+z)^2 like curvature but stays out of the curvature map, Ox (w = -2/3)
+    // as (1+z); such rows carry no tangents
+    const double Os = ncol >= 7 ? p[5] : 0.0, Ox = ncol >= 7 ? p[6] : 0.0;
     for (int i = 0; i < NREC; i++) rec[i] = 0;
     int st = ST_OK, kind = 0;
-    const int K = ncol - 1;
-    bool finite = isfinite(H0) && isfinite(Om) && isfinite(OL) && isfinite(Or) && isfinite(Ok);
+    const int K = ncol >= 7 ? 0 : ncol - 1;
+    bool finite = isfinite(H0) && isfinite(Om) && isfinite(OL) && isfinite(Or) && isfinite(Ok) &&
+                  isfinite(Os) && isfinite(Ox);
     int n = Or > 0 ? 4 : 3;
     if (!finite || !(H0 > 0) || Or < 0 || (n == 3 && !(Om > 0))) st = ST_INVALID;
     cd z[4];
-    double alpha[5] = {OL, 0.0, Ok, Om, Or};
+    double alpha[5] = {OL, Ox, Ok + Os, Om, Or};
     double an = alpha[n];
     double c[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
     c[n] = 1.0;
@@ -447,8 +452,8 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
     rec[RF_DH] = LCDM_C_KMS * iH0;
     rec[RF_TH] = LCDM_HUBBLE_GYR * iH0;
     rec[RF_KIND] = kind;
-    // N = sqrt(E^2(0) / alpha_n): E^2(0) = Om + OL + Or + Ok, exactly 1 under the closure
-    const double S0 = ncol == 4 ? 1.0 : Om + OL + Or + Ok;
+    // N = sqrt(E^2(0) / alpha_n): E^2(0) = Om + OL + Or + Ok (+ Os + Ox), exactly 1 under the closure
+    const double S0 = ncol == 4 ? 1.0 : Om + OL + Or + Ok + Os + Ox;
     const double iOm = ddiv(1.0, Om);
     const double nrm = n == 4 ? sqrt(S0) : sqrt(S0 * iOm);
     const double inrm = ddiv(1.0, nrm);
