@@ -280,8 +280,26 @@ typedef struct { double Om, OL, Or, Ok, Os, Ox; } cosmo_t;
  * [3 + 5*iw + ig]: -(1/2) w(a) g(a) Q^-3/2 for g = dQ/dOm = a, dQ/dOL = a^4,
  *                  dQ/dOr = 1, dQ/dOk = dQ/dOs = a^2, dQ/dOx = a^3 (Leibniz
  *                  rule under the integral). */
+/* Q(a) by Horner's rule with the rounding error of each step carried along
+ * exactly (error-free sum and product; the compensated Horner scheme of
+ * Graillat, Langlois and Louvet): near the deep minimum of Q at the
+ * no-Big-Bang boundary (Fig. 1) its O(1) terms cancel to the small minimum
+ * value, and a plain evaluation would leave the integrand with a relative
+ * error of eps times their ratio. */
+static double q_of_a(const cosmo_t* c, double a) {
+    const double co[5] = {c->OL, c->Ox, c->Ok + c->Os, c->Om, c->Or};   /* highest power first */
+    double h = co[0], err = 0.0;
+    for (int k = 1; k < 5; k++) {
+        double p = h * a, ep = fma(h, a, -p);
+        double s = p + co[k], bb = s - p, es = (p - (s - bb)) + (co[k] - bb);
+        err = err * a + (ep + es);
+        h = s;
+    }
+    return h + err;
+}
+
 static void integrand(double a, const cosmo_t* c, double* out) {
-    double Q = c->Or + c->Om * a + (c->Ok + c->Os) * a * a + c->Ox * a * a * a + c->OL * a * a * a * a;
+    double Q = q_of_a(c, a);
     double iq = 1.0 / sqrt(Q), iq3 = iq / Q;
     double w[3] = {1.0, a, 1.0 / (a * a)};
     double g[5] = {a, a * a * a * a, 1.0, a * a, a * a * a};

@@ -3,7 +3,7 @@
 * Factorisation (3.2): E^2(x) = alpha_m prod_j (x - rho_j) with x = 1 + z, so
   the roots in z are r_j = rho_j - 1.  Roots are the eigenvalues of the
   companion matrix (the numerical route of Sec. 3, fn12), then polished by
-  Newton steps on the original polynomial.
+  Newton steps on the original polynomial with an exact (rational) residual.
 * App. A, eqs. (A.1)-(A.4): the derivatives of the roots with respect to the
   monic coefficients c_k solve  1 = C^T (dr/dc),  where row j of C holds the
   coefficients of prod_{i != j} (x - rho_i) (Vieta's formulae); here the
@@ -26,17 +26,35 @@ def poly_coeffs_x(params):
     return np.stack([OL, Ox, Ok + Os, Om, Or], axis=1)
 
 
-def _polish(coef_low, x, iters=4):
-    """Newton polishing of roots x (complex) of sum_k coef_low[k] x^k."""
-    dc = np.array([k * coef_low[k] for k in range(1, len(coef_low))])
-    for _ in range(iters):
-        p = np.polyval(coef_low[::-1], x)
-        dp = np.polyval(dc[::-1], x)
-        step = np.where(dp != 0, p / np.where(dp != 0, dp, 1), 0)
-        xn = x - step
-        better = np.abs(np.polyval(coef_low[::-1], xn)) <= np.abs(p)
-        x = np.where(better, xn, x)
-    return x
+def _polish(coef_low, x, iters=6):
+    """Newton's method on sum_k coef_low[k] x^k for each root x (complex),
+    with the residual p(x) and p'(x) evaluated exactly in rational arithmetic
+    (the float coefficients and the float iterate are exact rationals), so the
+    only rounding is that of the new iterate to double.  Near a double root
+    (the no-Big-Bang boundary, Fig. 1) a double-precision residual is all
+    rounding noise once |p'| is small; the exact one still converges to the
+    root of the stated polynomial, to within the rounding of its parts."""
+    from fractions import Fraction as F
+    c = [F(float(a)) for a in coef_low]
+    out = np.array(x, dtype=np.complex128)
+    for j in range(out.size):
+        xr, xi = F(float(out[j].real)), F(float(out[j].imag))
+        for _ in range(iters):
+            pr, pi, dr, di = c[-1], F(0), F(0), F(0)
+            for a in c[-2::-1]:                      # Horner, highest power first
+                dr, di = dr * xr - di * xi + pr, dr * xi + di * xr + pi
+                pr, pi = pr * xr - pi * xi + a, pr * xi + pi * xr
+            den = dr * dr + di * di
+            if den == 0:
+                break
+            sr = (pr * dr + pi * di) / den               # p / p'
+            si = (pi * dr - pr * di) / den
+            nr, ni = F(float(xr - sr)), F(float(xi - si))
+            if nr == xr and ni == xi:
+                break
+            xr, xi = nr, ni
+        out[j] = complex(float(xr), float(xi))
+    return out
 
 
 def roots_x(params, real_tol=1e-10):

@@ -88,3 +88,24 @@ def test_physicality_classification_agrees_with_q_min():
         rho, nroot = oracle.roots_x(np.array([[70, Om, OL, Or]]))
         _, nobb = oracle.classify_roots(rho, nroot)
         assert nobb[0] == (not workloads.has_big_bang(Om, OL, Or))
+
+
+def test_near_double_roots_to_the_last_bit():
+    """Near the no-Big-Bang boundary (Fig. 1) two roots of E^2 nearly coincide
+    (config-5 draws: delta <= 1e-6, pair separation ~1e-3): the polished
+    roots must still be those of the stated FP64 polynomial to within one
+    rounding of each part (40-digit mpmath polyroots), since the distances'
+    sensitivity to the pair's imaginary part grows like its inverse."""
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 40
+    s = workloads.precision_stress(B=40, n=1, seed=4)
+    P = s.params[1::2]
+    rho, nroot = oracle.roots_x(P)
+    coef = oracle.poly_coeffs_x(P)
+    for b in range(P.shape[0]):
+        ref = mp.polyroots([mp.mpf(float(c)) for c in coef[b, ::-1]], maxsteps=400, extraprec=400)
+        for r in ref:
+            rr, ri = float(mp.re(r)), float(mp.im(r))
+            j = np.argmin(np.abs(rho[b] - complex(rr, ri)))
+            assert abs(rho[b, j].real - rr) <= np.spacing(abs(rr)), (b, rho[b, j], r)
+            assert abs(rho[b, j].imag - ri) <= np.spacing(abs(ri)) + 1e-300, (b, rho[b, j], r)
