@@ -13,8 +13,10 @@
  *                                                       (Sec. 2.1.1; fn22)
  * The quartic E^2 of eq. (2.2) is factorised per cosmology (eq. 3.2, FP64) and
  * each integral is reduced to Carlson's R_F, R_J, R_D, R_C (eqs. 2.6-2.9),
- * evaluated by duplication.  Derivatives with respect to the parameters use
- * eqs. (2.10)-(2.12) and the root derivatives of App. A (eqs. A.1-A.4).
+ * evaluated by duplication.  Derivatives with respect to the parameters are
+ * carried through the duplication sequences as forward-mode tangents (the
+ * differentiated form of eqs. 2.6-2.9; eq. 2.10 for R_C) from the root
+ * derivatives of App. A (eqs. A.1-A.4).
  *
  * Conventions shared by every entry point
  *   params   [B][ncol] float64, row-major: (H0 [km/s/Mpc], Omega_m0,
@@ -25,11 +27,11 @@
  *            components that keep E^2 a quartic (fn4): Omega_s0 (w = -1/3,
  *            scaling as (1+z)^2 like curvature but outside the curvature map)
  *            and Omega_x0 (w = -2/3, scaling as (1+z)); every density is then
- *            explicit.  Seven-column rows carry no tangents: they are accepted
- *            by lcdm_distances, lcdm_distances_static, lcdm_gauss_loglike
- *            without grad, lcdm_roots without droots and lcdm_autotune
- *            without grad; every entry point that needs tangents or the
- *            per-row shift returns LCDM_ERR_UNSUPPORTED for them.
+ *            explicit and an independent direction of the gradients
+ *            (Jacobian columns H0, Om, OL, Or, Ok, Os, Ox).  The general
+ *            limits (lcdm_distances_between, lcdm_limits) and the redshift
+ *            derivatives (lcdm_gauss_loglike_dz, lcdm_distances_vjp_dz) take
+ *            four or five columns and return LCDM_ERR_UNSUPPORTED for seven.
  *   pairs    layout LCDM_LAYOUT_CSR: offsets[B+1] int64 (offsets[0] = 0,
  *            non-decreasing, offsets[B] = n), z[n]; row b holds pairs
  *            offsets[b] .. offsets[b+1]-1.  Empty rows are allowed.
@@ -59,12 +61,21 @@
  *              1 no Big Bang: a real root of E^2 at z >= 0 (Sec. 3, Fig. 1)
  *              2 invalid parameters (non-finite, H0 <= 0, Omega_r0 < 0, or
  *                Omega_m0 <= 0 when Omega_r0 == 0)
- *              3 degenerate roots (coincident roots or rho_A == 0)
+ *              3 degenerate roots (two roots coinciding exactly, other
+ *                than the cases below, or rho_A == 0)
  *              4 duplication did not converge / principal value not available
- *              5 root configuration not supported (two complex pairs, or
- *                the triple root at z = -1 of Omega_L0 = Omega_k0 = 0:
- *                Einstein-de Sitter, flat matter + radiation)
+ *              5 root configuration not supported (two complex pairs)
  *            and every output of such a cosmology is NaN.
+ *   triple root  Omega_L0 = Omega_k0 (+ Omega_s0) = Omega_x0 = 0 to within
+ *            the rounding of the closure (Einstein-de Sitter, flat matter +
+ *            radiation: E^2 = x^3 (Or x + Om), x = 1 + z): the roots are set
+ *            exactly and the values are computed as for any row (status 0);
+ *            the root derivatives of App. A are singular there, so the
+ *            gradient entries of such a row in the density directions are
+ *            NaN (the H0 entry is finite).
+ *   Omega_L0 = 0 with Omega_k0 != 0 (a double root at x = 0): values and
+ *            FP64 gradients as for any row; in FP32 the d / d Omega_L0 entry
+ *            is NaN (the root derivatives there exceed the FP32 range).
  *   z = 0    gives d = t = X = 0, mu = -inf; tangents of mu with respect to
  *            the Omega columns are 0 and d mu / d H0 = -5 / (H0 ln 10).
  *   gradient with respect to Omega_r0 of a radiationless cosmology

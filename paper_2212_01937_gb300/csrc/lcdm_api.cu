@@ -47,29 +47,38 @@ lcdm_status carve(void* ws, size_t ws_bytes, int64_t B, Carved& c) {
     return LCDM_OK;
 }
 
+// SM count of the current device, looked up once per device
+#define LCDM_MAX_DEVICES 64
+std::atomic<int> g_num_sms[LCDM_MAX_DEVICES];
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= LCDM_MAX_DEVICES) dev = 0;
+    return dev;
+}
+
 int num_sms() {
-    static int n = 0;
-    if (n == 0) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
+    const int dev = current_device();
+    int n = g_num_sms[dev].load();
+    if (n <= 0) {
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+        g_num_sms[dev].store(n);
     }
     return n;
 }
 
 const PairsTable& table(int prec, int K) {
-    static PairsTable t[2][3];
+    static PairsTable t[2][4];
     static std::once_flag once;
     std::call_once(once, [] {
-        t[0][0] = table_f64_k0(); t[0][1] = table_f64_k3(); t[0][2] = table_f64_k4();
-        t[1][0] = table_mix_k0(); t[1][1] = table_mix_k3(); t[1][2] = table_mix_k4();
+        t[0][0] = table_f64_k0(); t[0][1] = table_f64_k3(); t[0][2] = table_f64_k4(); t[0][3] = table_f64_k6();
+        t[1][0] = table_mix_k0(); t[1][1] = table_mix_k3(); t[1][2] = table_mix_k4(); t[1][3] = table_mix_k6();
     });
-    return t[prec][K == 0 ? 0 : (K == 3 ? 1 : 2)];
+    return t[prec][K == 0 ? 0 : (K == 3 ? 1 : (K == 4 ? 2 : 3))];
 }
 
-// tuned launch shapes: key (precision, K, WT, WX, layout, log2 npairs)
-typedef std::tuple<int, int, int, int, int, int> TuneKey;
+// tuned launch shapes: key (device, precision, K, WT, WX, layout, log2 npairs)
+typedef std::tuple<int, int, int, int, int, int, int> TuneKey;
 struct Tuned { int block, bps, lane_map; };
 std::map<TuneKey, Tuned> g_tuned;
 std::mutex g_tune_mu;
@@ -131,13 +140,11 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
     a.sigma = sigma;
     a.grad = grad;
     a.loglike = loglike;
-    // rows with the further components (7 columns) have no tangent slots
-    if (tangents && opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;
     P.prec = opts->precision == LCDM_FP64 ? 0 : 1;
     P.K = tangents ? opts->ncol - 1 : 0;
     P.wt = wt;
     P.wx = wx;
-    P.key = TuneKey(P.prec, P.K, wt, wx, opts->layout, log2_bucket(P.npairs));
+    P.key = TuneKey(current_device(), P.prec, P.K, wt, wx, opts->layout, log2_bucket(P.npairs));
     return LCDM_OK;
 }
 
@@ -247,7 +254,6 @@ lcdm_status pairs_common(const double* params, int64_t B, const int64_t* offsets
                               ((size_t)LCDM_STATIC_MAX_COSMOLOGIES * NREC * sizeof(float2) + 255) / 256 * 256)
 static __device__ __align__(256) unsigned char g_static_ws[LCDM_STATIC_WS_BYTES];
 
-#define LCDM_MAX_DEVICES 64
 static void* g_static_ptr[LCDM_MAX_DEVICES];
 static std::mutex g_static_mu;
 
@@ -627,7 +633,6 @@ lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64
         (n > 0 && !z) || !cot || !grad || !cosmo_status || nchunks < 1 || nchunks > LCDM_HOST_MAX_CHUNKS)
         return LCDM_ERR_INVALID;
     if (offsets[0] != 0 || offsets[B] != n) return LCDM_ERR_INVALID;
-    if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // no tangent slots for 7-column rows
     for (int64_t r = 0; r < B; r++)
         if (offsets[r + 1] < offsets[r]) return LCDM_ERR_INVALID;
     const int ncol = opts->ncol;
@@ -714,7 +719,6 @@ lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes)
 lcdm_status lcdm_roots(const double* params, int64_t B, const lcdm_opts* opts, double* roots, double* droots,
                        int32_t* kind, int32_t* cosmo_status, void* ws, size_t ws_bytes, cudaStream_t stream) {
     if (!opts_ok(opts) || !params || !cosmo_status || B <= 0) return LCDM_ERR_INVALID;
-    if (droots && opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // no tangent slots for 7-column rows
     Carved cv;
     lcdm_status st = carve(ws, ws_bytes, B, cv);
     if (st != LCDM_OK) return st;

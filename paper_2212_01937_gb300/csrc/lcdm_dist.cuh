@@ -2,16 +2,11 @@
 // scalar S: a plain number (values only) or Dual<T,K> (values and tangents
 // with respect to the density parameters).
 //
-// Carlson integrals enter through carlson_any / rc_any.  Their tangents use
-//   dR_F/dx_m = -R_D(..x_m..)/6                                (eq. 2.10)
-//   dR_J/dx_m = (R_J - R_D(..x_m..)) / (2 (p - x_m))            (eq. 2.11)
-//   dR_J/dp   = 3/2 { (p^2 R_F - 2 p R_G + sqrt(x1 x2 x3))
-//                     / (p prod(p - x_i)) - sum 1/(p - x_i) R_J/3 } (eq. 2.12,
-//               with R_G(x1,x2,x3) where the printed formula shows R_D; R_G is
-//               formed from the three R_D by 6 R_G = sum_m x_m (e1 - x_m) R_D_m)
-// and, for R_D itself, dR_D(x,y,z)/dx = (R_D(x,y,z) - R_D(y,z,x)) / (2 (z - x))
-// with the special-argument derivative from homogeneity (degree -3/2).  All
-// R_D, R_J and R_F values come from one shared duplication sequence.
+// Carlson integrals enter through carlson_any / rc_any.  Their tangents are
+// carried through one shared duplication sequence as dual numbers (see
+// carlson_any); R_C's tangents use dR_F/dx_m = -R_D(..x_m..)/6 (eq. 2.10) with
+// R_C(x, y) = R_F(x, y, y).  All R_D, R_J and R_F values come from one shared
+// duplication sequence.
 //
 // Cauchy principal values (Sec. 2.2) for negative p or y:
 //   (q+z) R_J(x,y,z,-q) = (s-z) R_J(x,y,z,s) - 3 R_F + 3 sqrt(xyz/(xy+sq)) R_C(xy+sq, sq),
@@ -22,9 +17,6 @@
 
 namespace lcdm {
 
-template <class P> struct PairVal;
-template <class T, int K> struct PairVal<CPair<Dual<T, K> > > { typedef CPair<T> type; };
-template <class T, int K> struct PairVal<RPair<Dual<T, K> > > { typedef RPair<T> type; };
 
 // ---------------------------------------------------------------- values ----
 template <class T> LCDM_HD T rc_any(T x, T y, int* fail) {
@@ -105,32 +97,21 @@ template <class T, int K> LCDM_HD Dual<T, K> rc_any(const Dual<T, K>& x, const D
     return rc_dual_pos(x, y, fail);
 }
 
-// Relative spread of the arguments below which the derivative formulas lose
-// too many digits (they divide by differences of the arguments): there the
-// tangents are carried through the duplication sequence itself.  In FP32 the
-// tangents always go through the duplication sequence: measured against the
-// oracle it is the more accurate of the two at every spread (the formulas'
-// divisions by argument differences cost 2-4 more digits in FP32), and a
-// warp then runs a single code path.
-template <class T> struct Spread;
-template <> struct Spread<float> {
-    static LCDM_HD float s0() { return 0.5f; }
-    enum { always_dup = 1 };
-};
-template <> struct Spread<double> {
-    static LCDM_HD double s0() { return 0.05; }
-    enum { always_dup = 0 };
-};
-
+// Tangents of R_F, R_D and R_J are carried through the duplication sequence
+// itself (dual numbers), in both precisions.  The derivative formulas
+// (2.10)-(2.12), applied once after a plain duplication, divide by
+// differences of the arguments: they lose digits wherever two arguments are
+// close (every pair at low z, most pairs of a typical batch) or where two
+// roots of E^2 nearly coincide.  Measured in FP64 against the Leibniz-rule
+// oracle, the formulas left d t / d theta at 2e-2 for Omega_L0 = 1e-12 (a
+// near-double root at rho = 0) and d X / d Omega_r0 at 3e-5 for
+// Omega_r0 = 1e-12, where the dual tangents give 5e-14 and 4e-13.  Only
+// R_C's tangents use (2.10) (R_C(x, y) = R_F(x, y, y), no differences).
 template <int NJ, bool NEED_RD1, bool WANT_DJ, class T, int K, class PD>
 LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h, Dual<T, K>& RF,
                          Dual<T, K>& RD1, Dual<T, K>* RJ, int* fail, Dual<T, K>* DJ = 0) {
     typedef Dual<T, K> D;
-    typedef typename PairVal<PD>::type PT;
-    const T xv = x1.v;
-    const PT prv = pval(pr);
     D tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1], hh[NJ > 0 ? NJ : 1];
-    T trv[NJ > 0 ? NJ : 1];
     bool pv[NJ > 0 ? NJ : 1];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
@@ -146,95 +127,15 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h
             tr[j] = p;
             hh[j] = h[j];
         }
-        trv[j] = tr[j].v;
     }
-    // spread of the arguments around their mean
-    T mu = xv + psum(prv);
-#pragma unroll
-    for (int j = 0; j < NJ; j++) mu = mu + trv[j];
-    mu = mu * cst<T>(1.0 / (3 + NJ));
-    T dev2 = (xv - mu) * (xv - mu), pd2 = pdev2(prv, mu);
-    if (sval(pd2) > sval(dev2)) dev2 = pd2;
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-        T dj = (trv[j] - mu) * (trv[j] - mu);
-        if (sval(dj) > sval(dev2)) dev2 = dj;
-    }
-    T lim = Spread<T>::s0() * mu;
-    // The choice is made for all lanes that run together (either result is
-    // valid for every lane): a warp then runs one of the two paths, not both.
-    const bool close = Spread<T>::always_dup || group_any(sval(dev2) < sval(lim * lim));
     D Jd[NJ > 0 ? NJ : 1];
-    if (close) {
-        // tangents through the duplication sequence (arguments nearly equal)
-        DupResult<D, NJ, PD> R = carlson_dup<D, NJ, NEED_RD1 || WANT_DJ, PD, WANT_DJ, false>(
-            x1, pr, tr, fail, hh[NJ > 0 ? NJ - 1 : 0]);
-        RF = R.RF;
-        RD1 = R.RD1;
+    DupResult<D, NJ, PD> R = carlson_dup<D, NJ, NEED_RD1 || WANT_DJ, PD, WANT_DJ, false>(
+        x1, pr, tr, fail, hh[NJ > 0 ? NJ - 1 : 0]);
+    RF = R.RF;
+    RD1 = R.RD1;
 #pragma unroll
-        for (int j = 0; j < NJ; j++) Jd[j] = R.RJ[j];
-        if constexpr (WANT_DJ) *DJ = R.DJ;
-    } else {
-        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, WANT_DJ, true>(xv, prv, trv, fail, hh[NJ > 0 ? NJ - 1 : 0].v);
-        // R_F, eq. (2.10)
-        RF.v = R.RF;
-#pragma unroll
-        for (int k = 0; k < K; k++) RF.d[k] = (R.RD1 * x1.d[k] + pdot_k(R.RDp, pr, k)) * cst<T>(-1.0 / 6.0);
-        // R_D(x2, x3, x1): dR_D(x,y,z)/dx = (R_D(x,y,z) - R_D(y,z,x)) / (2 (z - x)); x1 by homogeneity
-        if (NEED_RD1 || WANT_DJ) {
-            PT dpair = pscale(prsub(R.RD1, R.RDp) / prsub(xv, prv), cst<T>(0.5));
-            T d1 = (cst<T>(-1.5) * R.RD1 - pdot(prv, dpair)) / xv;
-            RD1.v = R.RD1;
-#pragma unroll
-            for (int k = 0; k < K; k++) RD1.d[k] = d1 * x1.d[k] + pdot_k(dpair, pr, k);
-        }
-        if (NJ > 0) {
-            // 6 R_G = sum_m x_m (e1 - x_m) R_D_m
-            T RG = (xv * psum(prv) * R.RD1 + pdot(R.RDp, prv * padd(pswap(prv), xv))) * cst<T>(1.0 / 6.0);
-            T sq3 = ssqrt(xv) * pprod(psqrt(prv));
-#pragma unroll
-            for (int j = 0; j < NJ; j++) {
-                const T pt = trv[j], J = R.RJ[j], hv = hh[j].v;
-                const PT ipp = prcp(prsub(pt, prv));
-                // dR_J/dx_m for the pair members, eq. (2.11)
-                PT dpair = pscale(prsub(J, R.RDp) * ipp, cst<T>(0.5));
-                // (p - x1) dR_J/dp from eq. (2.12), multiplied through by (p - x1)
-                T hdp = cst<T>(1.5) * ((pt * pt * R.RF - cst<T>(2.0) * pt * RG + sq3) * pprod(ipp) / pt
-                                       - (cst<T>(1.0) + hv * psum(ipp)) * J * cst<T>(1.0 / 3.0));
-                // (d/dx1 + d/dp) R_J from homogeneity (degree -3/2); then
-                // dR_J = (d1 + dp) R_J dx1 + sum dR_J/dx_m dx_m + dR_J/dp d(p - x1)
-                T diag = (cst<T>(-1.5) * J - pdot(prv, dpair) - hdp) / xv;
-                T dph = hdp / hv;
-                Jd[j].v = J;
-#pragma unroll
-                for (int k = 0; k < K; k++) Jd[j].d[k] = diag * x1.d[k] + pdot_k(dpair, pr, k) + dph * hh[j].d[k];
-                if (WANT_DJ && j == NJ - 1 && !pv[j]) {
-                    // Delta = (R_J(x1 + h) - R_D(x2,x3,x1)) / h and its tangent from the
-                    // divided differences of eqs. (2.11)-(2.12):
-                    //  dDelta/dx_m = [Delta (x1 - x_m) - (R_D1 - R_Dm)] / (2 (p - x_m)(x1 - x_m))
-                    //  dDelta/dx1  = [-3/2 Delta - sum x_m dDelta/dx_m - dR_J/dp] / x1
-                    //  h dDelta/dh = dR_J/dp - Delta,  dR_J/dp = -Delta/2 + 3/2 Br
-                    const T Dl = R.DJ;
-                    PT xm = prsub(xv, prv);
-                    PT dxm = pscale((pscale(xm, Dl) - prsub(R.RD1, R.RDp)) / (prsub(pt, prv) * xm), cst<T>(0.5));
-                    const T S0 = psum(xm), P0 = pprod(xm);
-                    const T beta = cst<T>(1.0) / xv + (S0 + hv) / P0 + hv * (S0 + hv) / (xv * P0);
-                    const T Br = -(R.RD1 * cst<T>(1.0 / 3.0)) * beta / (cst<T>(1.0) + hv * beta)
-                                 + ((cst<T>(2.0) * xv + hv) * R.RF - cst<T>(2.0) * RG) * pprod(ipp) / pt
-                                 - psum(ipp) * J * cst<T>(1.0 / 3.0);
-                    const T dpR = cst<T>(-0.5) * Dl + cst<T>(1.5) * Br;
-                    const T d1 = (cst<T>(-1.5) * Dl - pdot(prv, dxm) - dpR) / xv;
-                    const T dhh = cst<T>(1.5) * (Br - Dl);
-                    D dd;
-                    dd.v = Dl;
-#pragma unroll
-                    for (int k = 0; k < K; k++)
-                        dd.d[k] = d1 * x1.d[k] + pdot_k(dxm, pr, k) + dhh * (hh[j].d[k] / hv);
-                    *DJ = dd;
-                }
-            }
-        }
-    }
+    for (int j = 0; j < NJ; j++) Jd[j] = R.RJ[j];
+    if constexpr (WANT_DJ) *DJ = R.DJ;
     // principal values (the tracks ran at s_j) and the divided difference fallback
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
@@ -286,7 +187,7 @@ template <class S> LCDM_HD S phi_rc(const S& w, int* fail) {
 template <class S, class PS, bool WT, bool WX>
 LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
                                const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, const S& qA,
-                               const S& qB, const PS& qP, const S& nrm, S& Ichi, S& It, S& IX, int* fail) {
+                               const S& qB, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX, int* fail) {
     typedef typename Base<S>::type T;
     const T one = cst<T>(1.0), third = cst<T>(1.0 / 3.0);
     const T z2 = z * z;
@@ -299,8 +200,9 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     //   u_AB = N (n_A n_B + n_P n_P*),  u_AP = N (n_P n_A + n_P* n_B),
     // N = Y~_A Y_B |Y_P|^2 = sqrt(E^2(0)).  The tangents of n_j are z dq_j / (2 n_j),
     // so the arguments' tangents vanish with z without cancellation.
+    // (wP = 1 + z q_P is formed by the caller: it cancels near z = Re r_P)
     S nA = ssqrt(one + qA * z), nB = ssqrt(one + qB * z);
-    PS nP = psqrt(padd(pscale(qP, z), one));
+    PS nP = psqrt(wP);
     S uAB = nrm * (nA * nB + pprod(nP));
     PS uAP = pscale(pscale(nP, nA) + pscale(pswap(nP), nB), nrm);
     S x1 = uAB * uAB;
@@ -318,9 +220,20 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     carlson_any<NJ, WX, WX>(x1, pr, p, RF, RD1, RJ, fail, &DJ);
     Ichi = RF * (z + z);                               // eq. (3.7)
     if (WT) {                                          // eq. (3.8), i = A
-        S kq5 = (x1 + p[jt]) * (one + z) / ((one + epsA) * (one + epsA * (one + z)));
-        S ks5 = kq5 + mA * pprod(rhoP) * rhoB * z2;
-        It = (rc_any(ks5, kq5, fail) - epsA * RF - mA * (one + epsA * rhoB) * ppPA * RJ[jt] * (z2 * third)) * (z + z);
+        // R_C(s_A5^2, q_A5^2) scaled by eps_A (homogeneity) is R_C(k s5, k q5) =
+        // k^-1/2 R_C(s5, q5) with k = (1+z) / cA, cA = (1 + eps_A)(1 + eps_A (1+z)).
+        // The part of k^-1/2 linear in eps_A is combined with -eps_A R_F: the two
+        // cancel as z -> 0, and so do their tangents, which carry
+        // d eps_A / d Or ~ 1 / Om.  With sqrt(cA) - 1 = eps_A (2 + z + eps_A (1+z)) / (sqrt(cA) + 1):
+        //   R_C(k s5, k q5) - eps_A R_F = RC' + eps_A [RC' (2 + z + eps_A (1+z)) / (sqrt(cA) + 1) - R_F],
+        // RC' = (1+z)^-1/2 R_C(s5, q5), and the bracket is O(z).
+        const T izh = one / ssqrt(one + z);
+        S cA = (one + epsA) * (one + epsA * (one + z));
+        S q5 = x1 + p[jt];
+        S s5 = q5 + mA * pprod(rhoP) * rhoB * z2 * cA * (izh * izh);
+        S RCp = rc_any(s5, q5, fail) * izh;
+        S Bk = RCp * ((cst<T>(2.0) + z + epsA * (one + z)) / (ssqrt(cA) + one)) - RF;
+        It = (RCp + epsA * Bk - mA * (one + epsA * rhoB) * ppPA * RJ[jt] * (z2 * third)) * (z + z);
     }
     if (WX) {                                          // eq. (3.9), i = B, l = A
         // The l = A part of (3.9), rho_A G, is a sum of O(1) terms that cancel to
@@ -357,7 +270,7 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
 
 template <class S, class PS, bool WT, bool WX>
 LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, const S& YA, const PS& YP,
-                             const S& amh, const S& qA, const PS& qP, const S& nrm, S& Ichi, S& It, S& IX,
+                             const S& amh, const S& qA, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX,
                              int* fail) {
     typedef typename Base<S>::type T;
     const T one = cst<T>(1.0);
@@ -369,7 +282,7 @@ LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, 
     // ratios n_j = X_j / Y_j = sqrt(1 + z q_j) as in the quartic:
     //   u_A = N (n_A + n_P n_P*),  u_P = N (n_P + n_P* n_A),  N = Y_A |Y_P|^2
     S nA = ssqrt(one + qA * z);
-    PS nP = psqrt(padd(pscale(qP, z), one));
+    PS nP = psqrt(wP);   // wP = 1 + z q_P, formed by the caller
     S uA = nrm * (nA + pprod(nP));
     PS uP = pscale(nP + pscale(pswap(nP), nA), nrm);
     S x1 = uA * uA;

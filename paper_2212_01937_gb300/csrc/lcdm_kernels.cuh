@@ -31,15 +31,16 @@ enum RecField {
     RF_AMH, RF_OK, RF_H0, RF_DH, RF_TH, RF_KIND,
     // quartic big-root quantities: lam = Or, a_A = -lam A, m_A = lam rho_A, eps_A = -1/rho_A, rho_A
     RF_LAM, RF_AA, RF_MA, RF_EPSA, RF_RHOA,
-    // tangents (4 slots each: Om, OL, Or, Ok)
-    RF_DA = 19, RF_DB = 23, RF_DPRE = 27, RF_DPIM = 31, RF_DAMH = 35, RF_DOK = 39,
-    RF_DLAM = 43, RF_DAA = 47, RF_DMA = 51, RF_DEPSA = 55, RF_DRHOA = 59,
+    // tangents (RF_KT slots each: Om, OL, Or, Ok, Os, Ox; the first ncol - 1 used)
+    RF_DA = 19, RF_DB = 25, RF_DPRE = 31, RF_DPIM = 37, RF_DAMH = 43, RF_DOK = 49,
+    RF_DLAM = 55, RF_DAA = 61, RF_DMA = 67, RF_DEPSA = 73, RF_DRHOA = 79,
     // q_j = -1/r_j for A, B and the pair (the two real members for kinds 1/3),
     // and the scale N = sqrt(E^2(0) / alpha_n) of the Carlson arguments
-    RF_QA = 63, RF_QB, RF_QPRE, RF_QPIM, RF_NRM,
-    RF_DQA = 68, RF_DQB = 72, RF_DQPRE = 76, RF_DQPIM = 80, RF_DNRM = 84,
-    NREC = 88
+    RF_QA = 85, RF_QB, RF_QPRE, RF_QPIM, RF_NRM,
+    RF_DQA = 90, RF_DQB = 96, RF_DQPRE = 102, RF_DQPIM = 108, RF_DNRM = 114,
+    NREC = 120
 };
+enum { RF_KT = 6 };   // tangent slots per field: at most six density directions
 
 enum CosmoStatus {
     ST_OK = 0, ST_NO_BIG_BANG = 1, ST_INVALID = 2, ST_DEGENERATE = 3, ST_NOCONV = 4, ST_UNSUPPORTED = 5
@@ -112,6 +113,22 @@ template <class T> LCDM_HD T recv(const double* rd, const float2* rf, int i);
 template <> LCDM_HD double recv<double>(const double* rd, const float2*, int i) { return rd[i]; }
 template <> LCDM_HD float recv<float>(const double*, const float2* rf, int i) { return rf[i].x; }
 
+// 1 + z q for a record field q.  It cancels where z q is near -1 (for the
+// complex pair near z = Re r_P, which lies at z > 0 close to the no-Big-Bang
+// boundary), so in FP32 q enters with its low word (hi, lo from the FP64
+// record) and the sum is formed in double-float arithmetic before it is
+// rounded once; FP64 rounds once by the fused multiply-add.
+template <class T> LCDM_HD T one_plus_qz(const double* rd, const float2* rf, int i, T z);
+template <> LCDM_HD double one_plus_qz<double>(const double* rd, const float2*, int i, double z) {
+    return fma(rd[i], z, 1.0);
+}
+template <> LCDM_HD float one_plus_qz<float>(const double*, const float2* rf, int i, float z) {
+    const float qh = rf[i].x, ql = rf[i].y;
+    const float p = qh * z, e1 = fmaf(qh, z, -p);   // qh z = p + e1 exactly
+    const df64 s = two_sum(1.0f, p);
+    return s.hi + (s.lo + fmaf(ql, z, e1));
+}
+
 // Build the root quantities in scalar S and evaluate the integrals.
 template <class T, int K, bool WT, bool WX> struct PairEval {
     typedef typename std::conditional<(K > 0), Dual<T, K>, T>::type S;
@@ -149,8 +166,13 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
         S Pre = val(rd, rf, RF_PRE, RF_DPRE), Pim = val(rd, rf, RF_PIM, RF_DPIM);
         S qA = val(rd, rf, RF_QA, RF_DQA), nrm = val(rd, rf, RF_NRM, RF_DNRM);
         S qPre = val(rd, rf, RF_QPRE, RF_DQPRE), qPim = val(rd, rf, RF_QPIM, RF_DQPIM);
+        // w_P = 1 + z q_P (its tangent z dq_P), the first member's real part
+        // by one_plus_qz
+        S wre = qPre * z, wim = qPim * z;
+        if constexpr (K > 0) wre.v = one_plus_qz<T>(rd, rf, RF_QPRE, z);
+        else wre = one_plus_qz<T>(rd, rf, RF_QPRE, z);
         if (kind == 0 || kind == 2) {
-            CPair<S> P = mkcp(mkcx<S>(Pre, Pim)), qP = mkcp(mkcx<S>(qPre, qPim));
+            CPair<S> P = mkcp(mkcx<S>(Pre, Pim)), wP = mkcp(mkcx<S>(wre, wim));
             Cx<S> yv;
             yv.re = val(rd, rf, RF_YPRE, RF_YPRE);
             yv.im = val(rd, rf, RF_YPIM, RF_YPIM);
@@ -173,12 +195,15 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
                 quartic_integrals<S, CPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
                                                        val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
                                                        val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, qA,
-                                                       val(rd, rf, RF_QB, RF_DQB), qP, nrm, Ichi, It, IX, fail);
+                                                       val(rd, rf, RF_QB, RF_DQB), wP, nrm, Ichi, It, IX, fail);
             } else {
-                cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, qP, nrm, Ichi, It, IX, fail);
+                cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
             }
         } else {
-            RPair<S> P = mkrp<S>(Pre, Pim), qP = mkrp<S>(qPre, qPim);
+            wim = wim + cst<T>(1.0);
+            if constexpr (K > 0) wim.v = one_plus_qz<T>(rd, rf, RF_QPIM, z);
+            else wim = one_plus_qz<T>(rd, rf, RF_QPIM, z);
+            RPair<S> P = mkrp<S>(Pre, Pim), wP = mkrp<S>(wre, wim);
             RPair<S> YP = mkrp<S>(yval(rd, rf, RF_YPRE, Pre), yval(rd, rf, RF_YPIM, Pim));
             if (kind == 1) {
                 S B = val(rd, rf, RF_B, RF_DB);
@@ -186,9 +211,9 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
                 quartic_integrals<S, RPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
                                                        val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
                                                        val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, qA,
-                                                       val(rd, rf, RF_QB, RF_DQB), qP, nrm, Ichi, It, IX, fail);
+                                                       val(rd, rf, RF_QB, RF_DQB), wP, nrm, Ichi, It, IX, fail);
             } else {
-                cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, qP, nrm, Ichi, It, IX, fail);
+                cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
             }
         }
     }

@@ -47,5 +47,7 @@ PairsTable table_f64_k4();
 PairsTable table_mix_k0();
 PairsTable table_mix_k3();
 PairsTable table_mix_k4();
+PairsTable table_f64_k6();
+PairsTable table_mix_k6();
 
 }  // namespace lcdm

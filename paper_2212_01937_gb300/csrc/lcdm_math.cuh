@@ -267,13 +267,6 @@ template <class T> LCDM_HD T pdot(const CPair<T>& c, const CPair<T>& x) {
     return cst<T>(2.0) * (c.c.re * x.c.re - c.c.im * x.c.im);
 }
 template <class T> LCDM_HD T pdot(const RPair<T>& c, const RPair<T>& x) { return c.a * x.a + c.b * x.b; }
-// sum over members of c_m * (tangent k of x_m)
-template <class T, int K> LCDM_HD T pdot_k(const CPair<T>& c, const CPair<Dual<T, K> >& x, int k) {
-    return cst<T>(2.0) * (c.c.re * x.c.re.d[k] - c.c.im * x.c.im.d[k]);
-}
-template <class T, int K> LCDM_HD T pdot_k(const RPair<T>& c, const RPair<Dual<T, K> >& x, int k) {
-    return c.a * x.a.d[k] + c.b * x.b.d[k];
-}
 // values of a dual pair
 template <class T, int K> LCDM_HD CPair<T> pval(const CPair<Dual<T, K> >& p) { return mkcp(mkcx<T>(p.c.re.v, p.c.im.v)); }
 template <class T, int K> LCDM_HD RPair<T> pval(const RPair<Dual<T, K> >& p) { return mkrp<T>(p.a.v, p.b.v); }
@@ -549,7 +542,11 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
             }
         }
         x1 = (x1 + lam) * cst<T>(0.25);
-        pr = pscale(padd(pr, lam), cst<T>(0.25));
+        // pair members: y_a + lam = (s_a + s1)(s_a + s_b) with s = sqrt(y), a
+        // product of sums of numbers with non-negative real parts, so no
+        // cancellation when y lies near the negative real axis (there
+        // y + |s|^2 = s (s + conj s) is small: near the no-Big-Bang boundary)
+        pr = pscale(padd(sp, s1), psum(sp) * cst<T>(0.25));
 #pragma unroll
         for (int j = 0; j < NJ; j++) p[j] = (p[j] + lam) * cst<T>(0.25);
         f = f * cst<T>(0.25);

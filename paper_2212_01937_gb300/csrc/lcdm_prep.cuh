@@ -45,6 +45,60 @@ LCDM_HD void horner(const double* c, int n, cd x, cd& p, cd& dp) {
     for (int k = n - 1; k >= 0; k--) { dp = cadd(cmul(dp, x), p); p = cadd(cmul(p, x), cmk(c[k], 0)); }
 }
 
+// Error-free transformations: Knuth's sum, and the product by the fused
+// multiply-add (a b = p + e exactly).
+LCDM_HD void two_sum_d(double a, double b, double& s, double& e) {
+    s = a + b;
+    const double bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+LCDM_HD void two_prod_d(double a, double b, double& p, double& e) {
+    p = a * b;
+    e = fma(a, b, -p);
+}
+
+// p(x) = sum_k a[k] x^k (degree n) and p'(x) at complex x by the compensated
+// Horner scheme (Graillat, Langlois and Louvet): the rounding error of every
+// Horner step is carried, exactly, into a second Horner recurrence, so the
+// value is as accurate as if it had been evaluated in twice the working
+// precision.  Newton's method on it then finds a root to the last bit even
+// where p' is small, as at the near-double roots of the no-Big-Bang boundary.
+LCDM_HD void horner_comp(const double* a, int n, cd x, cd& p, cd& dp) {
+    cd h = cmk(a[n], 0), q = cmk(0, 0);
+    dp = cmk(0, 0);
+#pragma unroll 1
+    for (int k = n - 1; k >= 0; k--) {
+        dp = cadd(cmul(dp, x), h);
+        double p1, e1, p2, e2, p3, e3, p4, e4, s1, e5, s2, e6, t1, e7;
+        two_prod_d(h.re, x.re, p1, e1);
+        two_prod_d(h.im, x.im, p2, e2);
+        two_prod_d(h.re, x.im, p3, e3);
+        two_prod_d(h.im, x.re, p4, e4);
+        two_sum_d(p1, -p2, s1, e5);
+        two_sum_d(p3, p4, s2, e6);
+        two_sum_d(s1, a[k], t1, e7);
+        q = cadd(cmul(q, x), cmk(((e1 - e2) + e5) + e7, (e3 + e4) + e6));
+        h = cmk(t1, s2);
+    }
+    p = cadd(h, q);
+}
+
+// Newton steps on the polynomial with the given (not normalised) coefficients,
+// evaluated by horner_comp; a step is kept only while |p| decreases.
+LCDM_HD void polish_root(const double* a, int n, cd& x) {
+    cd p, dp;
+    horner_comp(a, n, x, p, dp);
+#pragma unroll 1
+    for (int it = 0; it < 3; it++) {
+        if ((dp.re == 0 && dp.im == 0) || (p.re == 0 && p.im == 0)) return;
+        const cd xn = csub(x, cdiv(p, dp));
+        cd pn, dpn;
+        horner_comp(a, n, xn, pn, dpn);
+        if (!(cnorm(pn) < cnorm(p))) return;
+        x = xn; p = pn; dp = dpn;
+    }
+}
+
 // Single-precision elementary functions for the starting circles only (no
 // accuracy needed there): the fast hardware approximations on the device.
 LCDM_HD float flog(float x) {
@@ -118,7 +172,7 @@ LCDM_HD void start_points(const double* c, int n, cd* z) {
 // or once the corrections stop shrinking (rounding level of a near-multiple
 // root); one Newton step per root at the end.  On return every lane of the
 // group holds all n roots in z.
-template <int G> __device__ void group_roots(const double* c, int n, bool active, cd* z) {
+template <int G> __device__ void group_roots(const double* c, const double* alpha, int n, bool active, cd* z) {
     constexpr int R = 4 / G;   // roots per lane
     const unsigned full = 0xffffffffu;
     const int s = threadIdx.x & (G - 1);
@@ -187,6 +241,18 @@ template <int G> __device__ void group_roots(const double* c, int n, bool active
         for (int r = 0; r < R; r++)
             if (isfinite(zr[r]) && isfinite(zi[r])) { zre[r] = zr[r]; zim[r] = zi[r]; }
     }
+    // Single precision can merge a complex pair of nearly double roots (near
+    // the no-Big-Bang boundary) into two points on the real axis, and for a
+    // real polynomial the iteration keeps real approximations real.  A small
+    // imaginary offset of alternating sign (far above double precision, far
+    // below the root spacing) lets the double-precision sweeps move them back
+    // into the complex plane; real roots return to the axis.
+#pragma unroll
+    for (int r = 0; r < R; r++) {
+        const int j = r * G + s;
+        const double m = fabs(zre[r]) + fabs(zim[r]);
+        if (fabs(zim[r]) < 1e-6 * m) zim[r] += ((j & 1) ? -1e-6 : 1e-6) * m;
+    }
     {
         int settled = 0;
         double prev = 1e300;
@@ -227,22 +293,20 @@ template <int G> __device__ void group_roots(const double* c, int n, bool active
             }
             if (!done) {
                 if (worst < 1e-30) { if (++settled >= 1) done = true; }
-                else if (it >= 4 && worst >= 0.25 * prev) done = true;
+                else if (it >= 4 && worst >= 0.25 * prev && worst < 1e-24) done = true;
                 prev = worst;
             }
             if (__all_sync(full, done)) break;
         }
     }
-    // Newton polishing
+    // Newton polishing on the original coefficients (the monic ones carry the
+    // rounding of the division by alpha_n), evaluated by the compensated scheme
 #pragma unroll
     for (int r = 0; r < R; r++) {
         if (!active || r * G + s >= n) continue;
-        cd zj = cmk(zre[r], zim[r]), p, dp;
-        horner(c, n, zj, p, dp);
-        if (dp.re == 0 && dp.im == 0) continue;
-        cd zn = csub(zj, cmul(p, crcp(dp))), pn, dpn;
-        horner(c, n, zn, pn, dpn);
-        if (cnorm(pn) <= cnorm(p)) { zre[r] = zn.re; zim[r] = zn.im; }
+        cd zj = cmk(zre[r], zim[r]);
+        polish_root(alpha, n, zj);
+        zre[r] = zj.re; zim[r] = zj.im;
     }
 #pragma unroll
     for (int k = 0; k < 4; k++)
@@ -250,16 +314,10 @@ template <int G> __device__ void group_roots(const double* c, int n, bool active
                       : cmk(__shfl_sync(full, zre[k / G], k % G, G), __shfl_sync(full, zim[k / G], k % G, G));
 }
 
-LCDM_HD void polish_real(const double* c, int n, double& x) {
-    #pragma unroll 1
-    for (int k = 0; k < 3; k++) {
-        double p = c[n], dp = 0;
-        for (int j = n - 1; j >= 0; j--) { dp = dp * x + p; p = p * x + c[j]; }
-        if (dp == 0) return;
-        double xn = x - ddiv(p, dp), pn = c[n];
-        for (int j = n - 1; j >= 0; j--) pn = pn * xn + c[j];
-        if (fabs(pn) <= fabs(p)) x = xn; else return;
-    }
+LCDM_HD void polish_real(const double* alpha, int n, double& x) {
+    cd r = cmk(x, 0.0);
+    polish_root(alpha, n, r);
+    x = r.re;
 }
 
 // Record of one cosmology from its parameter row p[ncol] = (H0, Om, OL, Or[, Ok]);
@@ -270,11 +328,11 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
     double Ok = ncol >= 5 ? p[4] : 1.0 - Om - OL - Or;
     // the further components of fn4 (7-column rows): Os (w = -1/3) scales as
     // (1+z)^2 like curvature but stays out of the curvature map, Ox (w = -2/3)
-    // as (1+z); such rows carry no tangents
+    // as (1+z); with them every density is an independent direction
     const double Os = ncol >= 7 ? p[5] : 0.0, Ox = ncol >= 7 ? p[6] : 0.0;
     for (int i = 0; i < NREC; i++) rec[i] = 0;
     int st = ST_OK, kind = 0;
-    const int K = ncol >= 7 ? 0 : ncol - 1;
+    const int K = ncol - 1;
     bool finite = isfinite(H0) && isfinite(Om) && isfinite(OL) && isfinite(Or) && isfinite(Ok) &&
                   isfinite(Os) && isfinite(Ox);
     int n = Or > 0 ? 4 : 3;
@@ -289,13 +347,32 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
         for (int k = 0; k <= n; k++) c[k] = alpha[k] * ian;
         c[n] = 1.0;
     }
-    group_roots<G>(c, n, active && st == ST_OK, z);   // every lane, outside any divergent branch
+    // A triple root at rho = 0 (x = 1 + z = 0): OL = Ox = Ok + Os = 0 to within
+    // the rounding of the closure, so that E^2 = x^3 (Or x + Om) (flat matter +
+    // radiation; Einstein-de Sitter when Or = 0).  The root iteration cannot
+    // separate a triple root (its error would be of order eps^(1/3)), so the
+    // roots are set exactly: rho = 0 three times and rho_A = -Om/Or.  The
+    // reductions (3.7)-(3.9) / (B.1)-(B.3) then hold with the repeated roots
+    // (the factors d_ij that vanish only multiply terms that drop out).  The
+    // root derivatives of App. A are singular at a multiple root, so the
+    // tangent slots of such a row are NaN (no gradient).
+    const double dtol = 8.0 * 2.220446049250313e-16 * (fabs(Om) + fabs(Or) + fabs(OL) + fabs(Ok) + 1.0);
+    const bool triple0 = st == ST_OK && fabs(OL) <= dtol && fabs(Ox) <= dtol && fabs(Ok + Os) <= dtol;
+    group_roots<G>(c, alpha, n, active && st == ST_OK && !triple0, z);   // every lane, outside any divergent branch
+    if (triple0) {
+        z[0] = cmk(n == 4 ? -Om / Or : 0.0, 0.0);
+        for (int i = 1; i < 4; i++) z[i] = cmk(0.0, 0.0);
+    }
     if (st == ST_OK) {
         // classification: real when the imaginary part is negligible
         int nreal = 0, ir[4], ic[4], ncx = 0;
         #pragma unroll 1
         for (int i = 0; i < n; i++) {
-            if (fabs(z[i].im) <= 1e-12 * cabs_(z[i])) { z[i].im = 0; polish_real(c, n, z[i].re); ir[nreal++] = i; }
+            if (triple0 || fabs(z[i].im) <= 1e-12 * cabs_(z[i])) {
+                z[i].im = 0;
+                if (!triple0) polish_real(alpha, n, z[i].re);
+                ir[nreal++] = i;
+            }
             else ic[ncx++] = i;
         }
         #pragma unroll 1
@@ -333,7 +410,7 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
             if (n == 4) rho[nr++] = Bv;
             rho[nr++] = P1;
             rho[nr++] = cpair ? cmk(P1.re, -P1.im) : P2;
-            if (A.re == 0.0) st = st == ST_OK ? ST_DEGENERATE : st;   // division by rho_A in eq. (3.8)
+            if (A.re == 0.0 && !triple0) st = st == ST_OK ? ST_DEGENERATE : st;   // division by rho_A in eq. (3.8)
             rec[RF_A] = A.re - 1.0;
             rec[RF_B] = (n == 4 ? Bv.re : 1.0) - 1.0;
             if (cpair) { rec[RF_PRE] = P1.re - 1.0; rec[RF_PIM] = P1.im; }
@@ -346,9 +423,9 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
             // Summed over the coefficients c_i = alpha_i / alpha_n of the monic
             // polynomial this is
             //   d rho_j / d theta_k = -(dE^2/dtheta_k)(rho_j) / (alpha_n prod_{m != j} (rho_j - rho_m)),
-            // with dE^2/dOm = x^3, dE^2/dOL = 1, dE^2/dOr = x^4, dE^2/dOk = x^2, and
-            // -x^2 added to the first three under the closure.
-            cd dr[4][4];
+            // with dE^2/dOm = x^3, dE^2/dOL = 1, dE^2/dOr = x^4, dE^2/dOk = dE^2/dOs = x^2,
+            // dE^2/dOx = x, and -x^2 added to the first three under the closure.
+            cd dr[4][RF_KT];
             #pragma unroll 1
             for (int j = 0; j < nr; j++) {
                 const cd x = rho[j], x2 = cmul(x, x), x3 = cmul(x2, x), x4 = cmul(x3, x);
@@ -357,11 +434,11 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
                 for (int m2 = 0; m2 < nr; m2++)
                     if (m2 != j) e2p = cmul(e2p, csub(x, rho[m2]));
                 const bool degenerate = e2p.re == 0 && e2p.im == 0;
-                if (degenerate) st = (st == ST_OK) ? ST_DEGENERATE : st;
-                const cd inv = degenerate ? cmk(0, 0) : crcp(e2p);
+                if (degenerate && !triple0) st = (st == ST_OK) ? ST_DEGENERATE : st;
+                const cd inv = degenerate ? cmk(nan(""), nan("")) : crcp(e2p);
                 const double cl = ncol == 4 ? 1.0 : 0.0;
-                const cd g[4] = {csub(x3, cmul(cmk(cl, 0), x2)), csub(cmk(1, 0), cmul(cmk(cl, 0), x2)),
-                                 csub(x4, cmul(cmk(cl, 0), x2)), x2};
+                const cd g[RF_KT] = {csub(x3, cmul(cmk(cl, 0), x2)), csub(cmk(1, 0), cmul(cmk(cl, 0), x2)),
+                                     csub(x4, cmul(cmk(cl, 0), x2)), x2, x2, x};
                 #pragma unroll 1
                 for (int k = 0; k < K; k++) {
                     cd d = cmul(g[k], inv);
@@ -379,15 +456,16 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
                 rec[RF_EPSA] = -irA;
                 rec[RF_RHOA] = rA;
                 // Tangents of m_A = lam rho_A = y from the scaled quartic
-                //   F(y) = y^4 + Om y^3 + Ok Or y^2 + OL Or^3 = Or^3 E^2(rho_A) = 0,
+                //   F(y) = y^4 + Om y^3 + (Ok + Os) Or y^2 + Ox Or^2 y + OL Or^3 = Or^3 E^2(rho_A) = 0,
                 // dy = -(dF/dtheta) / (dF/dy), a ratio of O(1) terms: in the Or
                 // direction rho_A d lam and lam d rho_A are each O(Om/Or) and cancel.
                 // a_A = -lam (rho_A - 1) = -y + lam.
-                const double y = Or * rA;
-                const double iFy = ddiv(1.0, y * y * (4.0 * y + 3.0 * Om) + 2.0 * Ok * Or * y);
+                const double y = Or * rA, Oks = Ok + Os;
+                const double iFy = ddiv(1.0, y * y * (4.0 * y + 3.0 * Om) + 2.0 * Oks * Or * y + Ox * Or * Or);
                 const double cl = ncol == 4 ? 1.0 : 0.0, FOk = Or * y * y;
-                const double Fth[4] = {y * y * y - cl * FOk, Or * Or * Or - cl * FOk,
-                                       Ok * y * y + 3.0 * OL * Or * Or - cl * FOk, FOk};
+                const double Fth[RF_KT] = {y * y * y - cl * FOk, Or * Or * Or - cl * FOk,
+                                           Oks * y * y + 2.0 * Ox * Or * y + 3.0 * OL * Or * Or - cl * FOk, FOk, FOk,
+                                           Or * Or * y};
                 #pragma unroll 1
                 for (int k = 0; k < K; k++) {
                     double dl = (k == 2) ? 1.0 : 0.0, dA = dr[0][k].re;

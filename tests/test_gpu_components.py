@@ -1,7 +1,9 @@
 """Seven-column rows (the further components of fn4, w = -1/3 and -2/3):
-forward distances and the magnitude log-likelihood through the C ABI against
-the oracle; tangent-requiring calls are refused.  Tolerances as for the
-five-column path (test_gpu_parity.py)."""
+forward distances, the magnitude log-likelihood, and the derivatives with
+respect to all six densities (Om, OL, Or, Ok, Os, Ox, each independent)
+through the C ABI against the oracle (its Leibniz-rule gradients
+differentiate Os and Ox as well).  Tolerances as for the five-column path
+(test_gpu_parity.py)."""
 import numpy as np
 import pytest
 import torch
@@ -9,7 +11,7 @@ import torch
 import oracle
 from paper_2212_01937_gb300 import workloads
 
-from test_gpu_parity import TOL32, TOL64, _check, _t
+from test_gpu_parity import COLS, TOL32, TOL64, _check, _t, jac_tol
 
 pytestmark = pytest.mark.gpu
 
@@ -57,7 +59,38 @@ def test_components_loglike_and_refusals(lib):
     bound = np.array([np.sum(2 * np.abs(m[rows == b] - mu[rows == b] + 19.3) * 1e-5 / 0.01 + 1e-6)
                       for b in range(P.shape[0])])
     assert np.all(np.abs(got - want) <= bound), np.abs(got - want) / bound
-    with pytest.raises(RuntimeError):
-        lib.distances_vjp(_t(P), _t(z32), {"mu": _t(np.ones_like(z32))}, _t(offs))
-    with pytest.raises(RuntimeError):
-        lib.gauss_loglike(_t(P), _t(z32), _t(m), _t(offs), grad=True)
+    # the gradient of the log-likelihood: r/sigma^2 d mu / d theta summed per row
+    _, J = oracle.quad_distances(P, z32.astype(np.float64), offs, grad=True)
+    r = (m.astype(np.float64) - mu + 19.3) / 0.1
+    gw = np.array([((r[rows == b] / 0.1)[:, None] * J[rows == b, 5, :]).sum(axis=0) for b in range(P.shape[0])])
+    res = lib.gauss_loglike(_t(P), _t(z32), _t(m), _t(offs), M=-19.3, sigma=0.1, grad=True, precision="fp32")
+    torch.cuda.synchronize()
+    gg = res["grad"].cpu().numpy()
+    cols = np.ones(P.shape[1], dtype=bool)
+    for b in range(P.shape[0]):
+        c = cols.copy()
+        if P[b, 3] == 0:
+            c[3] = False                      # a radiationless row has no Omega_r0 direction
+            assert np.isnan(gg[b, 3])
+        assert np.max(np.abs(gg[b, c] - gw[b, c])) <= 1e-4 * np.abs(gw[b, c]).max(), (b, gg[b], gw[b])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_components_jacobian_vs_leibniz_oracle(lib, prec):
+    """Per-pair Jacobians with respect to (H0, Om, OL, Or, Ok, Os, Ox)."""
+    P, z, offs = _rows()
+    zin = z if prec == "fp64" else z.astype(np.float32)
+    zq = zin.astype(np.float64)
+    _, J = oracle.quad_distances(P, zq, offs, grad=True)
+    res = lib.distances_jac(_t(P), _t(zin), _t(offs), outputs=("d_C", "t", "X", "mu"), precision=prec)
+    torch.cuda.synchronize()
+    assert int(res["status"].abs().sum()) == 0
+    rows = np.repeat(np.arange(P.shape[0]), np.diff(offs))
+    rad = P[rows, 3] > 0
+    for n in (("d_C", "t", "X", "mu") if prec == "fp64" else ("d_C", "t", "mu")):
+        got = res["jac"][n].double().cpu().numpy()
+        want = J[:, COLS[n], :]
+        assert np.all(np.isnan(got[~rad, 3]))
+        got[~rad, 3] = want[~rad, 3] = 0.0
+        err = np.abs(got - want).max(axis=1) / np.abs(want).max(axis=1)
+        assert np.all(err <= jac_tol(prec, zq, n)), (prec, n, err.max())
