@@ -23,14 +23,14 @@ import math
 
 import torch
 
-from . import lcdm
+from . import lcdm, shard
 
 PARAM_NAMES = ("H0", "Om", "OL", "Or")
 
 
 class GaussianVI:
     def __init__(self, z, m_obs, centre, scale, M=-19.3, sigma=0.1, samples=256, lr=0.05,
-                 init_log_std=-1.0, precision="fp32", graph=True, betas=(0.9, 0.999), eps=1e-8):
+                 init_log_std=-1.0, precision="fp32", graph=True, betas=(0.9, 0.999), eps=1e-8, group=None):
         dev = z.device
         if not z.is_cuda:
             raise ValueError("z must be a CUDA tensor")
@@ -51,6 +51,11 @@ class GaussianVI:
         self.valid = torch.zeros((), **f64)
         self.call = lcdm.Call(self.params, z, layout="shared", precision=precision)
         self.m_obs = m_obs.to(device=dev, dtype=self.call.dtype).contiguous()
+        # with a process group, z and m_obs are this rank's share of the
+        # supernovae; the per-sample sums are added over the ranks by one
+        # all-reduce (shard.allreduce_loglike), and every rank must seed its
+        # CUDA generator alike so that all draw the same guide samples
+        self.group = group
         self.graph = None
         if graph:
             self._capture()
@@ -64,6 +69,8 @@ class GaussianVI:
         res = lcdm.gauss_loglike(self.params, None, self.m_obs, M=self.M, sigma=self.sigma, grad=True,
                                  call=self.call)
         ll, g = res["loglike"], res["grad"]
+        if self.group is not None:
+            shard.allreduce_loglike(ll, g, self.group)
         ok = (self.call.status == 0) & torch.isfinite(ll) & torch.isfinite(g).all(dim=1)
         w = ok.to(torch.float64)
         n = w.sum().clamp(min=1.0)
