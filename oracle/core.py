@@ -31,6 +31,9 @@ def _load():
         lib.oracle_carlson_batch.argtypes = [ctypes.c_int, ctypes.c_int64, dp, dp]
         lib.oracle_simpson.argtypes = [dp, ctypes.c_int, ctypes.c_double, ctypes.c_int64, dp]
         lib.oracle_set_mutation.argtypes = [ctypes.c_int]
+        lib.oracle_legendre_distances.argtypes = [dp, ctypes.c_int64, ctypes.c_int, ip, dp, ctypes.c_int64, dp,
+                                                  i32p, i32p, dp]
+        lib.oracle_hyp2f1_flat.argtypes = [ctypes.c_double, ctypes.c_double, dp, ctypes.c_int64, dp]
         _lib = lib
     return _lib
 
@@ -244,3 +247,66 @@ def simpson(param_row, z, n=1_000_000):
     res = np.zeros(3)
     _load().oracle_simpson(_dp(p), p.size, float(z), int(n), _dp(res))
     return res
+
+
+def _legendre_raw(params, z, offsets, rho, nroot, ijkl):
+    packed = np.zeros((params.shape[0], 4, 2))
+    packed[:, :, 0] = np.nan_to_num(rho.real)
+    packed[:, :, 1] = np.nan_to_num(rho.imag)
+    out = np.zeros((z.size, 2))
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    _load().oracle_legendre_distances(
+        _dp(params), params.shape[0], params.shape[1], offsets.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+        _dp(z), z.size, _dp(np.ascontiguousarray(packed)), np.ascontiguousarray(nroot, dtype=np.int32).ctypes.data_as(i32p),
+        np.ascontiguousarray(ijkl, dtype=np.int32).ctypes.data_as(i32p), _dp(out))
+    return out
+
+
+def legendre_assignment(params, zprobe=(0.5, 2.0, 8.0)):
+    """Root assignment (i, j, k, l) of eqs. (B.4)-(B.7) per cosmology.  The
+    formulas hold only for some orderings (App. B.2; the paper leaves the
+    quartic choice open): the first permutation, in lexicographic order,
+    whose comoving distance and time agree with the quadrature oracle to
+    1e-8 at the probe redshifts is taken (-1 everywhere when none does)."""
+    import itertools
+    from . import roots as _roots
+    params = np.ascontiguousarray(np.atleast_2d(params), dtype=np.float64)
+    rho, nroot = _roots.roots_x(params)
+    zp = np.asarray(zprobe, dtype=np.float64)
+    res = np.full((params.shape[0], 4), -1, dtype=np.int32)
+    for b in range(params.shape[0]):
+        m = int(nroot[b])
+        ref = quad_distances(params[b:b + 1], zp, np.array([0, zp.size]))
+        for perm in itertools.permutations(range(m)):
+            q = np.array(list(perm) + [0] * (4 - m), dtype=np.int32)
+            with np.errstate(all="ignore"):
+                got = _legendre_raw(params[b:b + 1], zp, np.array([0, zp.size], dtype=np.int64), rho[b:b + 1],
+                                    nroot[b:b + 1], q[None, :])
+            if np.all(np.isfinite(got)) and np.all(np.abs(got / ref[:, :2] - 1) < 1e-8):
+                res[b] = q
+                break
+    return res, (rho, nroot)
+
+
+def legendre_distances(params, z, offsets=None, assignment=None):
+    """Eqs. (B.4)-(B.7): d_C [Mpc] and t [Gyr] in Legendre's form (App. B.2),
+    F~ and Pi~ from Carlson's integrals (DLMF 19.25.5, 19.25.14), complex
+    FP64.  Returns [nnz, 2] (NaN for rows without a valid assignment)."""
+    params, z, offsets, B, ncol = _csr(params, z, offsets)
+    if assignment is None:
+        ijkl, (rho, nroot) = legendre_assignment(params)
+    else:
+        ijkl, (rho, nroot) = assignment
+    out = _legendre_raw(params, z, offsets, rho, nroot, ijkl)
+    rows = np.repeat(np.arange(B), np.diff(offsets))
+    out[ijkl[rows, 0] < 0] = np.nan
+    return out
+
+
+def hyp2f1_flat_distance(H0, Om, z):
+    """d_C [Mpc] of a flat radiationless cosmology by the hypergeometric
+    solution (Sec. 3.2.2; x 2F1(1/2, 1/3; 4/3; -(Om/OL) x^3) / sqrt(OL))."""
+    z = np.ascontiguousarray(z, dtype=np.float64).reshape(-1)
+    out = np.zeros(z.size)
+    _load().oracle_hyp2f1_flat(float(H0), float(Om), _dp(z), z.size, _dp(out))
+    return out

@@ -895,3 +895,111 @@ int oracle_simpson(const double* p, int ncol, double z, int64_t n, double* res) 
     res[2] = C_KMS / H0 * s[2] * h / 3.0;
     return 0;
 }
+
+/* ======================================================================== */
+/* Comparators of the speed study (Sec. 3.2.2, Fig. 3): the Legendre form  */
+/* of App. B.2 and the hypergeometric solution of the flat radiationless   */
+/* comoving distance.  FP64, plain; used for timing beside O1 and O2 and   */
+/* pinned against O1.                                                      */
+/* ======================================================================== */
+
+/* Legendre's integrals with c = csc^2 phi (App. B.2's tilde notation), from
+ * Carlson's (DLMF 19.25.5 and 19.25.14):
+ *   F~(c, m)    = R_F(c - 1, c - m, c),
+ *   Pi~(n, c, m) = F~(c, m) + (n/3) R_J(c - 1, c - m, c, c - n). */
+static cplx leg_F(cplx c, cplx m) { return oracle_rf(c - 1.0, c - m, c); }
+static cplx leg_Pi(cplx n, cplx c, cplx m) {
+    return leg_F(c, m) + n / 3.0 * oracle_rj(c - 1.0, c - m, c, c - n);
+}
+
+/* eqs. (B.4)-(B.5) (quartic, roots r[0..3] in z, assignment i j k l) and
+ * (B.6)-(B.7) (cubic, r[0..2], assignment i j k) for one pair, z1 -> z2;
+ * res = (chi H0/c, t H0) without the alpha_m^-1/2 prefactor, complex.  The
+ * bracket [f]_{z2}^{z1} is f(z1) - f(z2), as printed. */
+static void legendre_pair(const cplx* r, int nroot, const int* ijkl, double z1, double z2, cplx* chi, cplx* t) {
+    const int i = ijkl[0], j = ijkl[1], k = ijkl[2], l = ijkl[3];
+    if (nroot == 4) {
+        cplx m = (r[k] - r[j]) / (r[k] - r[i]) * (r[l] - r[i]) / (r[l] - r[j]);
+        cplx n = (1.0 + r[j]) / (1.0 + r[i]) * (r[l] - r[i]) / (r[l] - r[j]);
+        cplx c1 = (z1 - r[j]) / (z1 - r[i]) * (r[l] - r[i]) / (r[l] - r[j]);
+        cplx c2 = (z2 - r[j]) / (z2 - r[i]) * (r[l] - r[i]) / (r[l] - r[j]);
+        cplx den = csqrt((r[i] - r[k]) * (r[j] - r[l]));
+        *chi = 2.0 * (leg_F(c1, m) - leg_F(c2, m)) / den;
+        cplx b1 = (1.0 + r[i]) * leg_F(c1, m) - (r[i] - r[j]) * leg_Pi(n, c1, m);
+        cplx b2 = (1.0 + r[i]) * leg_F(c2, m) - (r[i] - r[j]) * leg_Pi(n, c2, m);
+        *t = 2.0 * (b1 - b2) / (den * (1.0 + r[i]) * (1.0 + r[j]));
+    } else {
+        cplx m = (r[k] - r[i]) / (r[j] - r[i]);
+        cplx n = -(1.0 + r[i]) / (r[j] - r[i]);
+        cplx c1 = (z1 - r[i]) / (r[j] - r[i]), c2 = (z2 - r[i]) / (r[j] - r[i]);
+        cplx den = csqrt(r[j] - r[i]);
+        *chi = 2.0 * (leg_F(c1, m) - leg_F(c2, m)) / den;
+        /* (B.7) with its prefactor read as 1/H0 (a time) */
+        *t = 2.0 * ((leg_F(c1, m) - leg_Pi(n, c1, m)) - (leg_F(c2, m) - leg_Pi(n, c2, m))) / (den * (1.0 + r[i]));
+    }
+}
+
+/* Batch: pairs of rows b with roots[b][4] (complex, in x = 1 + z as for O2),
+ * nroot[b] and assignment ijkl[b][4]; out[p][2] = (d_C [Mpc], t [Gyr]). */
+int oracle_legendre_distances(const double* params, int64_t B, int ncol, const int64_t* offsets, const double* z,
+                              int64_t nnz, const double* roots, const int32_t* nroot, const int32_t* ijkl,
+                              double* out) {
+    (void)nnz;
+    for (int64_t b = 0; b < B; b++) {
+        const double H0 = params[b * ncol], Om = params[b * ncol + 1], Or = params[b * ncol + 3];
+        cplx r[4];
+        for (int m = 0; m < 4; m++) r[m] = roots[(b * 4 + m) * 2] - 1.0 + I * roots[(b * 4 + m) * 2 + 1];
+        const int q[4] = {ijkl[4 * b], ijkl[4 * b + 1], ijkl[4 * b + 2], ijkl[4 * b + 3]};
+        const double pre = 1.0 / sqrt(nroot[b] == 4 ? Or : Om);
+        for (int64_t p = offsets[b]; p < offsets[b + 1]; p++) {
+            cplx chi, t;
+            legendre_pair(r, nroot[b], q, 0.0, z[p], &chi, &t);
+            out[2 * p] = creal(chi) * pre * C_KMS / H0;
+            out[2 * p + 1] = creal(t) * pre * HUBBLE_TIME_GYR / H0;
+        }
+    }
+    return 0;
+}
+
+/* Gauss's hypergeometric series 2F1(a, b; c; u) for 0 <= u <= 1/2. */
+static double hyp2f1_series(double a, double b, double c, double u) {
+    double term = 1.0, sum = 1.0;
+    for (int n = 0; n < 2000; n++) {
+        term *= (a + n) * (b + n) / ((c + n) * (n + 1.0)) * u;
+        sum += term;
+        if (fabs(term) <= 1e-17 * fabs(sum)) break;
+    }
+    return sum;
+}
+
+/* The flat radiationless comoving distance by the hypergeometric function
+ * (Sec. 3.2.2 and its ref. [2]):
+ *   int dx / sqrt(OL + Om x^3) = x 2F1(1/2, 1/3; 4/3; -(Om/OL) x^3) / sqrt(OL),
+ * with 2F1(1/2, 1/3; 4/3; -y) = (1+y)^(-1/3) 2F1(5/6, 1/3; 4/3; u),
+ * u = y/(1+y) (Pfaff, DLMF 15.8.1), summed directly for u <= 1/2 and through
+ * the connection to 1 - u (DLMF 15.8.4; c - a - b = 1/6) otherwise:
+ *   2F1(5/6, 1/3; 4/3; u) = G1 u^(-1/3) + G2 (1-u)^(1/6) 2F1(1/2, 1; 7/6; 1 - u),
+ *   G1 = G(4/3) G(1/6) / (G(1/2) G(1)),  G2 = G(4/3) G(-1/6) / (G(5/6) G(1/3)). */
+static double f21_flat(double y) {
+    const double u = y / (1.0 + y), v = 1.0 / (1.0 + y);   /* v = 1 - u, formed without cancellation */
+    double f;
+    if (u <= 0.5) {
+        f = hyp2f1_series(5.0 / 6.0, 1.0 / 3.0, 4.0 / 3.0, u);
+    } else {
+        const double G1 = tgamma(4.0 / 3.0) * tgamma(1.0 / 6.0) / (tgamma(0.5) * tgamma(1.0));
+        const double G2 = tgamma(4.0 / 3.0) * tgamma(-1.0 / 6.0) / (tgamma(5.0 / 6.0) * tgamma(1.0 / 3.0));
+        f = G1 * pow(u, -1.0 / 3.0) + G2 * pow(v, 1.0 / 6.0) * hyp2f1_series(0.5, 1.0, 7.0 / 6.0, v);
+    }
+    return pow(1.0 + y, -1.0 / 3.0) * f;
+}
+
+/* d_C [Mpc] of the flat radiationless cosmology (H0, Om, OL = 1 - Om) at z[n]. */
+int oracle_hyp2f1_flat(double H0, double Om, const double* z, int64_t n, double* out) {
+    const double OL = 1.0 - Om, w = Om / OL;
+    const double f1 = f21_flat(w);
+    for (int64_t p = 0; p < n; p++) {
+        const double x = 1.0 + z[p];
+        out[p] = (x * f21_flat(w * x * x * x) - f1) / sqrt(OL) * C_KMS / H0;
+    }
+    return 0;
+}
