@@ -337,6 +337,20 @@ const char* lcdm_status_string(int status);
 /* Number of kernels this library has launched in this process so far. */
 int64_t lcdm_launch_count(void);
 
+/* Issue-rate probes (no counterpart in the paper): the denominators of a
+ * roofline for the pair kernel, measured on the GPU at hand.  what = 0: FP32
+ * fused multiply-add; 1: FP32 reciprocal square root (the special-function
+ * unit that also serves division and square root); 2: FP64 fused
+ * multiply-add.  Launches blocks x threads threads (threads a multiple of 32,
+ * <= 1024), each running lcdm_probe_ops_per_thread(iters) operations of that
+ * kind in 8 independent chains, and writes one value per thread to out
+ * (device, blocks * threads floats, or doubles for what = 2).  Time the call
+ * with events on `stream`; rate = blocks * threads * ops / time.  Returns
+ * LCDM_ERR_INVALID for a bad shape or kind, before any launch. */
+int64_t lcdm_probe_ops_per_thread(int32_t iters);
+lcdm_status lcdm_probe(int32_t what, void* out, int32_t blocks, int32_t threads, int32_t iters,
+                       cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

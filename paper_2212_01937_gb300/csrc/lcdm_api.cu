@@ -94,6 +94,11 @@ struct Plan {
     int prec, K, wt, wx;
     int64_t npairs;
     TuneKey key;
+    // outputs wanted as values only while other outputs need tangents: the
+    // time coordinate and the absorption distance each run their own R_J
+    // track, whose tangents would be computed for nothing; such outputs are
+    // written by a second, tangent-free launch (split_mask: LCDM_T, LCDM_X bits)
+    int split_mask;
 };
 
 lcdm_status check_pairs_args(const double* params, int64_t B, const int64_t* offsets, const void* z, int64_t n,
@@ -134,6 +139,7 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
         if (used && i == LCDM_T) wt = 1;
         if (used && i == LCDM_X) wx = 1;
     }
+    P.split_mask = 0;
     if (mobs) { tangents = tangents || grad != nullptr; }
     a.mobs = mobs;
     a.M = M;
@@ -142,13 +148,58 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
     a.loglike = loglike;
     P.prec = opts->precision == LCDM_FP64 ? 0 : 1;
     P.K = tangents ? opts->ncol - 1 : 0;
+    if (P.K > 0) {
+        for (int i : {LCDM_T, LCDM_X}) {
+            if (a.out[i] && !a.jac[i] && !a.cot[i]) {
+                P.split_mask |= 1 << i;
+                if (i == LCDM_T) wt = 0;
+                if (i == LCDM_X) wx = 0;
+            }
+        }
+    }
     P.wt = wt;
     P.wx = wx;
     P.key = TuneKey(current_device(), P.prec, P.K, wt, wx, opts->layout, log2_bucket(P.npairs));
     return LCDM_OK;
 }
 
+lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s);
+
+// The plan's launches: the value-only outputs of split_mask first (K = 0,
+// their tracks only, no reductions), then the tangent launch without them.
 lcdm_status launch_plan(Plan& P, int block, int bps, int lane_map, cudaStream_t s) {
+    if (P.split_mask) {
+        Plan V = P;
+        PairArgs& v = V.args;
+        v.outmask = 0;
+        for (int i = 0; i < LCDM_NOUT; i++) {
+            v.jac[i] = nullptr;
+            v.cot[i] = nullptr;
+            if (!(P.split_mask & (1 << i))) v.out[i] = nullptr;
+            if (v.out[i]) v.outmask |= 1 << i;
+        }
+        v.mobs = nullptr;
+        v.grad = nullptr;
+        v.loglike = nullptr;
+        V.K = 0;
+        V.wt = (P.split_mask >> LCDM_T) & 1;
+        V.wx = (P.split_mask >> LCDM_X) & 1;
+        V.split_mask = 0;
+        std::get<2>(V.key) = 0;
+        std::get<3>(V.key) = V.wt;
+        std::get<4>(V.key) = V.wx;
+        lcdm_status st = launch_one(V, 0, 0, lane_map, s);
+        if (st != LCDM_OK) return st;
+        Plan T = P;
+        for (int i = 0; i < LCDM_NOUT; i++)
+            if (P.split_mask & (1 << i)) { T.args.out[i] = nullptr; T.args.outmask &= ~(1 << i); }
+        T.split_mask = 0;
+        return launch_one(T, block, bps, lane_map, s);
+    }
+    return launch_one(P, block, bps, lane_map, s);
+}
+
+lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s) {
     const PairsTable& t = table(P.prec, P.K);
     int idx = (P.wt ? 2 : 0) + (P.wx ? 1 : 0);
     if (block == 0 || bps == 0 || lane_map == LCDM_MAP_TUNED) {

@@ -89,7 +89,7 @@ LCDM_HD void polish_root(const double* a, int n, cd& x) {
     cd p, dp;
     horner_comp(a, n, x, p, dp);
 #pragma unroll 1
-    for (int it = 0; it < 3; it++) {
+    for (int it = 0; it < 2; it++) {
         if ((dp.re == 0 && dp.im == 0) || (p.re == 0 && p.im == 0)) return;
         const cd xn = csub(x, cdiv(p, dp));
         cd pn, dpn;
@@ -242,16 +242,31 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
             if (isfinite(zr[r]) && isfinite(zi[r])) { zre[r] = zr[r]; zim[r] = zi[r]; }
     }
     // Single precision can merge a complex pair of nearly double roots (near
-    // the no-Big-Bang boundary) into two points on the real axis, and for a
-    // real polynomial the iteration keeps real approximations real.  A small
-    // imaginary offset of alternating sign (far above double precision, far
-    // below the root spacing) lets the double-precision sweeps move them back
-    // into the complex plane; real roots return to the axis.
+    // the no-Big-Bang boundary) into two points on or near the real axis, and
+    // for a real polynomial the iteration keeps real approximations real.
+    // Two such approximations within 1e-3 of each other get imaginary
+    // offsets of opposite sign (far above double precision, far below the
+    // spacing), which lets the double-precision sweeps move them back into
+    // the complex plane if the roots are complex; real ones return to the axis.
+    {
+        double cr[4], ci[4];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        const int j = r * G + s;
-        const double m = fabs(zre[r]) + fabs(zim[r]);
-        if (fabs(zim[r]) < 1e-6 * m) zim[r] += ((j & 1) ? -1e-6 : 1e-6) * m;
+        for (int k = 0; k < 4; k++) {
+            cr[k] = G == 1 ? zre[k / G] : __shfl_sync(full, zre[k / G], k % G, G);
+            ci[k] = G == 1 ? zim[k / G] : __shfl_sync(full, zim[k / G], k % G, G);
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int j = r * G + s;
+            if (j >= n) continue;
+            const double m = fabs(cr[j]) + fabs(ci[j]);
+            if (!(fabs(ci[j]) < 1e-6 * m)) continue;
+#pragma unroll 1
+            for (int k = 0; k < n; k++) {
+                if (k == j || !(fabs(ci[k]) < 1e-6 * m)) continue;
+                if (fabs(cr[k] - cr[j]) < 1e-3 * m) { zim[r] += (j < k ? 1e-6 : -1e-6) * m; break; }
+            }
+        }
     }
     {
         int settled = 0;

@@ -64,6 +64,10 @@ def load():
     lib.lcdm_gauss_loglike_dz.argtypes = [_vp, i64, _vp, _vp, _vp, i64, dbl, dbl, _vp, _vp, _vp, _vp, _vp, op,
                                           _vp, sz, _vp]
     lib.lcdm_distances_vjp_dz.argtypes = [_vp, i64, _vp, _vp, i64, _VP6, _VP6, _vp, _vp, _vp, op, _vp, sz, _vp]
+    lib.lcdm_probe.argtypes = [i32, _vp, i32, i32, i32, _vp]
+    lib.lcdm_probe.restype = ctypes.c_int
+    lib.lcdm_probe_ops_per_thread.argtypes = [i32]
+    lib.lcdm_probe_ops_per_thread.restype = i64
     lib.lcdm_status_string.argtypes = [ctypes.c_int]
     lib.lcdm_status_string.restype = ctypes.c_char_p
     lib.lcdm_launch_count.restype = i64
@@ -92,6 +96,30 @@ def _stream(device):
 
 def launch_count():
     return int(load().lcdm_launch_count())
+
+
+def probe_rate(what, device, iters=2048, reps=5):
+    """Measured issue rate of one pipe (lcdm_probe): what = "ffma" (FP32
+    fused multiply-adds/s), "mufu" (FP32 reciprocal square roots/s) or
+    "dfma" (FP64 fused multiply-adds/s), over 8 resident 256-thread blocks
+    per SM, best of ``reps`` timed launches after one warm-up."""
+    kind = {"ffma": 0, "mufu": 1, "dfma": 2}[what]
+    it = iters if kind != 2 else max(1, iters // 32)
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
+    blocks, threads = 8 * sms, 256
+    out = torch.empty(blocks * threads, dtype=torch.float64 if kind == 2 else torch.float32, device=device)
+    lib = load()
+    best = None
+    for r in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        _check(lib.lcdm_probe(kind, _ptr(out), blocks, threads, it, _stream(device)))
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        if r > 0 and (best is None or ms < best):
+            best = ms
+    return blocks * threads * lib.lcdm_probe_ops_per_thread(it) / (best / 1e3)
 
 
 class Call:
