@@ -26,21 +26,37 @@ sys.path.insert(0, ROOT)
 METRIC = "distance+gradient pairs/sec (FP32 batched) vs plain FP64 forward, same GB300, ≤2e-6 rel"
 UNIT = "pairs/s"
 OUTPUTS = ("d_C", "t", "X", "mu")
-# Work of the dominant kernel per pair for this workload: FP32 floating-point
-# operations (FFMA counted as 2, FADD and FMUL as 1) executed per pair, from
-# an ncu capture of this kernel on this workload (its summary is under profiles/).
-FLOP_PER_PAIR = 5501.0
-# DRAM bytes (read + write) per launch of that kernel from the same capture
-# (None once the kernel has changed since the counters were taken).
-TRAFFIC_BYTES = 131349248
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+# Outputs that carry a cotangent in the timed step.  X is computed (a forward
+# output of the step) but not differentiated: its FP32 gradient is not within
+# the gradient bound for nearly empty open universes (eq. 3.9 with i = B, whose
+# terms are O(rho_B^2) and cancel; about 5 % of this batch's pairs), and the
+# FP64 path is the one to use where dX/dtheta is needed.
+COT_OUTPUTS = ("d_C", "t", "mu")
+# Algorithmic work per pair of the timed step (forward d_C, t, X, mu and the
+# adjoint of the cotangents on d_C, t, mu), counted by the oracle's operation
+# counter (oracle/opcount.py, `python -m oracle.opcount 1000`, 1000 sampled
+# pairs of this batch; its output is summarised under profiles/): real FP32
+# add/sub + mul, and div + sqrt + transcendental (the special-function unit).
+ALG_FLOP_PER_PAIR = 7033.1
+ALG_MUFU_PER_PAIR = 390.3
+# FP32 floating-point operations the kernel executes per pair (FFMA counted as
+# 2, FADD and FMUL as 1) and DRAM bytes (read + write) per launch, from an ncu
+# capture of this kernel on this workload (None until re-taken after a change
+# of the kernel).
+EXEC_FLOP_PER_PAIR = None
+TRAFFIC_BYTES = None
+# Derived peaks (unit counts x maximum SM clock): FP32 FMA, 152 SMs x 128 lanes
+# x 2 flops; special-function unit, 152 SMs x 16 per clock.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+MUFU_PEAK_GOPS = 152 * 16 * 2.07e9 / 1e9
 
 
 def base_config(b):
     """The workload description both arms report."""
     return {"workload": b.name + " (general LCDM+radiation+curvature batch: 4096 cosmologies x 1024 z)",
             "B": b.B, "n_per_row": 1024, "pairs_per_gpu": int(b.nnz), "outputs": list(OUTPUTS),
-            "gradient": "fused VJP w.r.t. (H0, Om, OL, Or), random cotangents on all outputs"}
+            "gradient": "fused VJP w.r.t. (H0, Om, OL, Or), random cotangents on d_C, t, mu (X is computed, "
+                        "not differentiated: its FP32 gradient misses the bound on ~5 % of the pairs)"}
 
 
 def workload(seed_offset=0):
@@ -128,22 +144,70 @@ def cpu_model():
 
 
 def cpu_carlson_rate(b, budget_s, seed=0):
-    """The Carlson oracle (O2, eqs. 3.7-3.9 / B.1-B.3 from the companion-matrix
-    roots; forward values only) pairs/s on one thread, on a random sample."""
+    """The Carlson oracle (O2, eqs. 3.7-3.9 / B.1-B.3; forward values only)
+    pairs/s on one thread, on a random sample.  The roots (per cosmology,
+    companion matrix and exact-residual polish) are computed before the timed
+    region: they are amortised over a row's pairs."""
     import oracle
+    from oracle import roots as oroots
     rng = np.random.default_rng(seed)
     def run(n):
         idx = np.sort(rng.choice(b.nnz, n, replace=False))
         rows = np.searchsorted(b.offsets, idx, side="right") - 1
         z = b.z[idx].astype(np.float32).astype(np.float64)
+        P = b.params[rows]
+        rr = oroots.roots_x(P)
+        perm = oroots.permutations(*rr)
         t0 = time.perf_counter()
-        oracle.carlson_distances(b.params[rows], z, np.arange(n + 1))
+        oracle.carlson_distances(P, z, np.arange(n + 1), roots=rr, perm=perm)
         return time.perf_counter() - t0
     n0 = min(2000, b.nnz)
     t = run(n0)
     n = int(min(max(n0, budget_s / max(t, 1e-9) * n0), 2_000_000, b.nnz))
     t = run(n)
     return n / t, n
+
+
+def fig3_comparator(nz=2000, budget_s=1.0):
+    """The speed study of Sec. 3.2.2 (Fig. 3) on one host thread: d_C (and t
+    where the method gives it) from z1 = 0 to each of nz redshifts
+    z ~ logU(1e-3, 1e3) for the flat (0.3, 0.7) setup without and with
+    Omega_r0 = 1e-5, by the Carlson oracle (eqs. 3.7-3.9 / B.1-B.3, complex
+    FP64), the Legendre form (eqs. B.4-B.7), the hypergeometric solution
+    (flat radiationless only) and adaptive quadrature (forward only).
+    Pairs/s of each, best of repeated calls within budget_s; the root
+    solve and the Legendre root assignment are per cosmology and excluded."""
+    import oracle
+    rng = np.random.default_rng(9)
+    z = np.sort(10.0 ** rng.uniform(-3, 3, nz))
+    off = np.array([0, nz], dtype=np.int64)
+    out = {"z": "logU(1e-3, 1e3), %d values, 1 thread" % nz}
+
+    def rate(f):
+        best, t_end = None, time.perf_counter() + budget_s
+        while True:
+            t0 = time.perf_counter()
+            f()
+            dt = time.perf_counter() - t0
+            best = dt if best is None else min(best, dt)
+            if time.perf_counter() > t_end:
+                return nz / best
+
+    from oracle import roots as oroots
+    for name, p in (("flat_radiationless", [70.0, 0.3, 0.7, 0.0]), ("flat_radiation_1e-5", [70.0, 0.3, 0.7, 1e-5])):
+        P = np.array([p])
+        rr = oroots.roots_x(P)
+        perm = oroots.permutations(*rr)
+        asg = oracle.legendre_assignment(P)
+        row = {"carlson": rate(lambda: oracle.carlson_distances(P, z, off, roots=rr, perm=perm)),
+               "legendre": rate(lambda: oracle.legendre_distances(P, z, off, assignment=asg)),
+               "quad": rate(lambda: oracle.quad_distances(P, z, off))}
+        if p[3] == 0.0:
+            row["hyp2f1"] = rate(lambda: oracle.hyp2f1_flat_distance(70.0, 0.3, z))
+        out[name] = {k: {"value": v, "unit": UNIT} for k, v in row.items()}
+    out["note"] = ("context for the paper's Fig. 3 (plotted, not tabulated); carlson and legendre give d_C, t "
+                   "(carlson also X), hyp2f1 d_C only, quad all three")
+    return out
 
 
 def _oracle_chunk(task):
@@ -186,16 +250,20 @@ def reference_arm(args):
     if rank != 0:
         return
     b = workload()
-    rates = []
+    rates, walls = [], []
     nsample, procs = 0, 1
     for step in range(args.warmup + args.steps):
         r, nsample, procs = cpu_oracle_rate_all(b, budget_s=min(20.0, 60.0 / max(1, args.steps + args.warmup)),
                                                 seed=step)
         if step >= args.warmup:
             rates.append(r)
+            walls.append(nsample / r)
     v = float(np.mean(rates))
+    # each step is a bounded random sample of the workload's pairs: the step
+    # time reported is the sample's measured wall time, not an extrapolation
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * b.nnz / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(walls)),
+            "pairs_per_step": int(nsample),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": base_config(b),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": procs, "kind": "oracle",
@@ -220,6 +288,8 @@ def main():
     ap.add_argument("--no-limits", action="store_true",
                     help="skip the general-limits and age/horizon timings")
     ap.add_argument("--no-bhm", action="store_true", help="skip the latent-redshift VI step timing")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-cosmology latency and full-size precision-stress lines")
     args = ap.parse_args()
     if args.impl == "reference":
         return reference_arm(args)
@@ -244,7 +314,7 @@ def main():
     offsets = torch.tensor(b.offsets, device=dev)
     z = torch.tensor(b.z, dtype=torch.float32, device=dev)
     g = torch.Generator(device="cpu").manual_seed(7 + rank)
-    cot = {n: torch.randn(npairs, generator=g).to(dev) for n in OUTPUTS}
+    cot = {n: torch.randn(npairs, generator=g).to(dev) for n in COT_OUTPUTS}
     call = lcdm.Call(params, z, offsets, precision="fp32")
     tune = None if args.no_autotune else lcdm.autotune(params, z, offsets, outputs=OUTPUTS, cot=cot,
                                                          precision="fp32")
@@ -316,14 +386,31 @@ def main():
     line = None
     if rank == 0:
         clocks = clock_summary(rows, local)
-        achieved = None if FLOP_PER_PAIR is None else FLOP_PER_PAIR * npairs / (pair_ms / 1e3) / 1e12
+        achieved = ALG_FLOP_PER_PAIR * npairs / (pair_ms / 1e3) / 1e12
+        mufu = ALG_MUFU_PER_PAIR * npairs / (pair_ms / 1e3) / 1e9
+        meas = {"ffma_tflops": 2 * lcdm.probe_rate("ffma", dev) / 1e12,
+                "mufu_gops": lcdm.probe_rate("mufu", dev) / 1e9,
+                "dfma_tflops": 2 * lcdm.probe_rate("dfma", dev) / 1e12,
+                "how": "lcdm_probe: 8 independent chains per thread, 8 x 256-thread blocks per SM, best of 5"}
         roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": None if achieved is None else achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": TRAFFIC_BYTES,
+                "algorithmic_ops_per_pair": {"flops": ALG_FLOP_PER_PAIR, "mufu": ALG_MUFU_PER_PAIR,
+                                             "source": "oracle/opcount.py, 1000 sampled pairs of this batch"},
+                "frac_algorithmic": achieved / FP32_PEAK_TFLOPS,
+                "frac_algorithmic_of_measured_ffma": achieved / meas["ffma_tflops"],
+                "executed_flops_per_pair": EXEC_FLOP_PER_PAIR,
+                "frac_executed": (None if EXEC_FLOP_PER_PAIR is None else
+                                  EXEC_FLOP_PER_PAIR * npairs / (pair_ms / 1e3) / 1e12 / FP32_PEAK_TFLOPS),
+                "mufu": {"achieved_gops": mufu, "peak_gops": MUFU_PEAK_GOPS, "frac": mufu / MUFU_PEAK_GOPS,
+                         "frac_of_measured": mufu / meas["mufu_gops"]},
+                "measured_peaks": meas,
                 "kernel": "pairs_kernel<FP32,K=3,t,X>", "kernel_ms": pair_ms, "prep_ms": prep_ms,
-                "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived, nominal clock)"}
+                "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived from unit counts and "
+                             "the maximum clock; MEASURED_PEAKS has HBM and bf16 only)"}
         extra = {}
         if not args.no_fp64_baseline:
-            extra = fp64_baselines(lcdm, params, offsets, b, dev)
+            extra = fp64_baselines(lcdm, params, offsets, b, dev, value)
+        extra["accuracy"] = step_accuracy(lcdm, b, params, z, offsets, cot, res, dev)
         cpu = None
         if not args.no_cpu_baseline:
             r1, n1 = cpu_oracle_rate(b, budget_s=6.0)
@@ -336,7 +423,9 @@ def main():
             rc, nc = cpu_carlson_rate(b, budget_s=3.0)
             cpu["carlson_forward_single_thread"] = {
                 "value": rc, "unit": UNIT, "cores": 1,
-                "sample": "%d random pairs, Carlson oracle forward only (no gradient), 1 thread" % nc}
+                "sample": "%d random pairs, Carlson oracle forward only (no gradient; roots outside the timed "
+                          "region), 1 thread" % nc}
+            cpu["fig3_comparator"] = fig3_comparator()
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -358,6 +447,9 @@ def main():
             line["limits_step"] = limits_rate(dev)
         if not args.no_bhm:
             line["bhm_step"] = bhm_step_rate(dev)
+        if not args.no_configs:
+            line["config1_fp64_latency"] = config1_rate(lcdm, dev)
+            line["config5_precision_stress"] = config5_rate(lcdm, dev)
         print(json.dumps(line))
     if dist:
         dist.barrier()
@@ -482,12 +574,12 @@ def between_step_rate(dev):
     z1 = torch.tensor(d.extra["z1"], device=dev)
     z = torch.tensor(d.z, dtype=torch.float32).to(dev)
     g = torch.Generator(device="cpu").manual_seed(11)
-    cot = {n: torch.randn(d.nnz, generator=g).to(dev) for n in OUTPUTS}
+    cot = {n: torch.randn(d.nnz, generator=g).to(dev) for n in COT_OUTPUTS}
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)
     f = lambda: lcdm.distances_between(params, z1, z, off, outputs=OUTPUTS, cot=cot, precision="fp32")
     ms = graph_ms(lambda: (flush.zero_(), f()), dev) - graph_ms(lambda: flush.zero_(), dev)
     return {"workload": d.name + " (z1 ~ U(0,3) per row, z2 = z1 + U(0,10)), FP32 fused VJP, "
-                                 "CUDA-graph replay, L2 flushed",
+                                 "CUDA-graph replay, L2 flushed (cotangents on d_C, t, mu)",
             "pairs_per_step": int(d.nnz), "ms_per_step": ms, "value": d.nnz / (ms / 1e3), "unit": UNIT}
 
 
@@ -505,36 +597,168 @@ def limits_rate(dev):
             "rows_per_step": d.B, "ms_per_step": ms, "value": d.B / (ms / 1e3), "unit": "rows/s"}
 
 
-def fp64_baselines(lcdm, params, offsets, b, dev):
-    """The denominators named by the metric: the plain FP64 forward kernel
-    launched once per cosmology, and the same kernel batched."""
+def fp64_baselines(lcdm, params, offsets, b, dev, headline):
+    """The denominators named by the metric, on the same GPU and batch: the
+    plain FP64 forward (d_C, t, X, mu) launched once per cosmology (4096
+    launches of lcdm_distances, every call's arguments and buffers prepared
+    beforehand, the launches replayed from one CUDA graph so that no host work
+    is timed), and the same forward batched in one launch.  The headline's
+    ratio to each is reported; the batched one is the honest denominator."""
+    import ctypes
     import torch
     z64 = torch.tensor(b.z, dtype=torch.float64, device=dev)
-    n = b.offsets[1] - b.offsets[0]
-    ws = lcdm.Call(params[:1], z64[:n], layout="dense", precision="fp64", block=128, blocks_per_sm=1).ws
+    n = int(b.offsets[1] - b.offsets[0])
     outs = ("d_C", "t", "X", "mu")
+    lib = lcdm.load()
+    calls = []
+    for r in range(b.B):
+        c = lcdm.Call(params[r:r + 1], z64[r * n:(r + 1) * n], layout="dense", precision="fp64", block=128,
+                      blocks_per_sm=1)
+        out, vp = c.out_buffers(outs)
+        calls.append((c, out, vp))
 
     def plain():
-        for r in range(b.B):
-            lcdm.distances(params[r:r + 1], z64[r * n:(r + 1) * n], None, outputs=outs, layout="dense",
-                           precision="fp64", block=128, blocks_per_sm=1, workspace=ws)
+        for c, out, vp in calls:
+            lib.lcdm_distances(*c.common(), vp, lcdm._ptr(c.status), *c.tail())
+
+    bc = lcdm.Call(params, z64, offsets, precision="fp64")
+    bout, bvp = bc.out_buffers(outs)
 
     def batched():
-        lcdm.distances(params, z64, offsets, outputs=outs, precision="fp64")
+        lib.lcdm_distances(*bc.common(), bvp, lcdm._ptr(bc.status), *bc.tail())
 
     res = {}
-    for name, f, reps in (("plain_per_cosmology", plain, 1), ("batched", batched, 3)):
-        f()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(reps):
-            f()
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / reps
-        res[name] = {"value": b.nnz / (ms / 1e3), "unit": UNIT, "ms_per_step": ms}
+    for name, f, reps in (("plain_per_cosmology", plain, 1), ("batched", batched, 5)):
+        ms = graph_ms(f, dev, reps=reps)
+        res[name] = {"value": b.nnz / (ms / 1e3), "unit": UNIT, "ms_per_step": ms,
+                     "headline_ratio": headline / (b.nnz / (ms / 1e3))}
+    res["plain_per_cosmology"]["how"] = ("4096 launches (root preparation + pair kernel each, 1024 pairs), "
+                                         "replayed from one CUDA graph")
+    res["batched"]["how"] = "one call over the whole batch, replayed from a CUDA graph"
+    res["headline_denominator"] = "batched"
     return {"fp64_forward_baseline": res}
+
+
+def step_accuracy(lcdm, b, params, z, offsets, cot, res, dev, nsample=3000):
+    """Accuracy of the timed step: its FP32 outputs on a random sample of
+    pairs and its per-cosmology gradient, against the FP64 GPU path on the
+    same inputs (the FP64 path is held to 1e-12 of the oracle by the tests).
+    Per-pair Jacobians of the sample (FP32 vs FP64) give the per-output
+    gradient errors, relative to the largest entry of each pair's row, and
+    the count of pairs above the stated bound (3e-5 + 2e-6/z; t 1e-4 + 2e-6/z;
+    X, which the step does not differentiate, 1e-3 + 2e-6/z)."""
+    import torch
+    rng = np.random.default_rng(5)
+    idx = np.sort(rng.choice(b.nnz, nsample, replace=False))
+    rows = np.searchsorted(b.offsets, idx, side="right") - 1
+    it = torch.tensor(idx, device=dev)
+    p_s = params[torch.tensor(rows, device=dev)]
+    z_s = z[it]
+    off_s = torch.arange(nsample + 1, device=dev)
+    names = ("d_C", "t", "X", "mu")
+    j64 = lcdm.distances_jac(p_s, z_s.double(), off_s, outputs=names, precision="fp64")
+    j32 = lcdm.distances_jac(p_s, z_s, off_s, outputs=names, precision="fp32")
+    zz = z_s.double().cpu().numpy()
+    acc = {"sample_pairs": nsample}
+    for n in names:
+        got = res[n][it].double().cpu().numpy()
+        want = j64[n].cpu().numpy()
+        if n == "mu":
+            fin = np.isfinite(want)
+            e = np.abs(got[fin] - want[fin])
+            acc["mu_abs"] = {"max": float(e.max()), "q99": float(np.quantile(e, 0.99))}
+        else:
+            e = np.abs(got / want - 1)
+            acc[n + "_rel"] = {"max": float(e.max()), "q99": float(np.quantile(e, 0.99))}
+        J32 = j32["jac"][n].double().cpu().numpy()
+        J64 = j64["jac"][n].cpu().numpy()
+        ej = np.abs(J32 - J64).max(axis=1) / np.abs(J64).max(axis=1)
+        c0 = {"t": 1e-4, "X": 1e-3}.get(n, 3e-5)
+        acc["d" + n + "_jac_rel"] = {"max": float(ej.max()), "q99": float(np.quantile(ej, 0.99)),
+                                     "bound": "%g + 2e-6/z" % c0,
+                                     "pairs_above_bound": int(np.count_nonzero(ej > c0 + 2e-6 / zz))}
+    g64 = lcdm.distances_vjp(params, z.double(), {k: v.double() for k, v in cot.items()}, offsets,
+                             precision="fp64")["grad"]
+    g32 = res["grad"]
+    eg = ((g32 - g64).abs().max(dim=1).values / g64.abs().max(dim=1).values).cpu().numpy()
+    acc["grad_vjp_rel_per_cosmology"] = {"max": float(eg.max()), "q99": float(np.quantile(eg, 0.99))}
+    acc["reference"] = "FP64 GPU path on the same inputs (z rounded to FP32)"
+    return acc
+
+
+def config1_rate(lcdm, dev):
+    """One flat radiationless cosmology (70, 0.3, 0.7), 10^4 redshifts
+    z ~ U(0.01, 2), FP64 d_C and mu, forward only (the cubic reduction):
+    microseconds per call, from a CUDA-graph replay (device time) and from
+    eager calls (with the binding's host work)."""
+    import torch
+    from paper_2212_01937_gb300 import workloads
+    d = workloads.flat_radiationless()
+    params = torch.tensor(d.params, device=dev)
+    z = torch.tensor(d.z, device=dev)
+    off = torch.tensor(d.offsets, device=dev)
+    call = lcdm.Call(params, z, off, precision="fp64")
+    lib = lcdm.load()
+    out, vp = call.out_buffers(("d_C", "mu"))
+    f = lambda: lib.lcdm_distances(*call.common(), vp, lcdm._ptr(call.status), *call.tail())
+    ms_graph = graph_ms(f, dev, reps=20)
+    for _ in range(3):
+        f()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(50):
+        f()
+    torch.cuda.synchronize()
+    ms_eager = (time.perf_counter() - t0) * 1e3 / 50
+    return {"workload": d.name + " (flat radiationless, z ~ U(0.01, 2)), FP64 d_C + mu, forward",
+            "us_per_call_device": ms_graph * 1e3, "us_per_call_eager": ms_eager * 1e3,
+            "pairs_per_call": int(d.nnz), "value": d.nnz / (ms_graph / 1e3), "unit": UNIT}
+
+
+def config5_rate(lcdm, dev, steps=5):
+    """Precision stress at full size: 10^4 cosmologies x 10^4 redshifts
+    (half within 1e-6 of flatness, half within 1e-6 of the no-Big-Bang
+    boundary), z ~ logU(1e-4, 1100), explicit Omega_k0; FP32 forward d_C, t,
+    X, mu in one launch (inputs 400 MB, larger than L2).  The error per
+    output on 2000 sampled pairs against the FP64 GPU path on the same z."""
+    import torch
+    from paper_2212_01937_gb300 import workloads
+    s = workloads.precision_stress()
+    params = torch.tensor(s.params, device=dev)
+    off = torch.tensor(s.offsets, device=dev)
+    z = torch.tensor(s.z.astype(np.float32), device=dev)
+    names = ("d_C", "t", "X", "mu")
+    call = lcdm.Call(params, z, off, precision="fp32")
+    lib = lcdm.load()
+    out, vp = call.out_buffers(names)
+    f = lambda: lib.lcdm_distances(*call.common(), vp, lcdm._ptr(call.status), *call.tail())
+    for _ in range(2):
+        f()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        f()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    rng = np.random.default_rng(3)
+    idx = torch.tensor(np.sort(rng.choice(s.nnz, 2000, replace=False)), device=dev)
+    rows = torch.searchsorted(off, idx, right=True) - 1
+    r64 = lcdm.distances(params[rows], z[idx].double(), torch.arange(2001, device=dev), outputs=names,
+                         precision="fp64")
+    err = {}
+    for n in names:
+        a, w = out[n][idx].double(), r64[n]
+        if n == "mu":
+            fin = torch.isfinite(w)
+            err["mu_abs_max"] = float((a[fin] - w[fin]).abs().max())
+        else:
+            err[n + "_rel_max"] = float((a / w - 1).abs().max())
+    return {"workload": s.name + " (precision stress, near-flat and near the no-Big-Bang boundary), FP32 forward "
+                                 "d_C, t, X, mu", "pairs_per_step": int(s.nnz), "ms_per_step": ms,
+            "value": s.nnz / (ms / 1e3), "unit": UNIT, "status_nonzero": int((call.status != 0).sum()),
+            "error_vs_fp64_gpu_2000_sampled": err}
 
 
 if __name__ == "__main__":

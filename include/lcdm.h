@@ -115,7 +115,18 @@ typedef struct {
     int32_t block;          /* threads per block (multiple of 32, <= 256); 0 = tuned */
     int32_t blocks_per_sm;  /* persistent blocks per SM; 0 = tuned               */
     int32_t lane_map;       /* pairs of a warp's range to lanes: LCDM_MAP_*      */
+    int32_t deterministic;  /* 1: per-cosmology sums reproducible bit for bit (see below) */
 } lcdm_opts;
+
+/* deterministic: the per-cosmology reductions (grad of lcdm_distances_vjp,
+ * loglike and grad of lcdm_gauss_loglike) add the partial sums of the warps
+ * that share a row in a fixed order (a second, small kernel), instead of
+ * FP64 atomics in arrival order, so that repeated calls with the same
+ * inputs, launch shape and device give the same bits.  Rows owned by one
+ * warp are summed in program order either way.  Needs the larger workspace
+ * that lcdm_workspace_size reports for it; honoured by lcdm_distances_vjp,
+ * lcdm_distances_jac, lcdm_gauss_loglike and lcdm_autotune, and refused
+ * (LCDM_ERR_UNSUPPORTED) by the other entry points that reduce. */
 
 /* lane_map: LCDM_MAP_TUNED takes the autotuner's choice for this workload
  * class, contiguous until it has run; LCDM_MAP_CONTIGUOUS gives the 32 lanes
@@ -126,7 +137,8 @@ typedef struct {
  * cache needs). */
 enum { LCDM_MAP_TUNED = 0, LCDM_MAP_CONTIGUOUS = 1, LCDM_MAP_INTERLEAVED = 2 };
 
-/* Workspace bytes needed for B cosmologies (per-cosmology root records). */
+/* Workspace bytes needed for B cosmologies (per-cosmology root records, and
+ * with opts->deterministic the warps' partial sums). */
 lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes);
 
 /* Root preparation alone (Sec. 3, eq. 3.2; App. A): roots of E^2 in z for

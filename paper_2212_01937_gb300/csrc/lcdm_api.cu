@@ -32,18 +32,36 @@ bool opts_ok(const lcdm_opts* o) {
            (o->precision == LCDM_FP64 || o->precision == LCDM_FP32_MIXED) &&
            o->layout >= LCDM_LAYOUT_CSR && o->layout <= LCDM_LAYOUT_SHARED && o->block >= 0 && o->block <= 256 &&
            (o->block % 32) == 0 && o->blocks_per_sm >= 0 && o->blocks_per_sm <= 64 && o->lane_map >= LCDM_MAP_TUNED &&
-           o->lane_map <= LCDM_MAP_INTERLEAVED;
+           o->lane_map <= LCDM_MAP_INTERLEAVED && (o->deterministic == 0 || o->deterministic == 1);
+}
+
+int num_sms();
+
+// Partial sums of the deterministic reduction: per launched warp, the sums
+// of its first and last rows (DET_NV values each) and those rows' indices.
+// At most 64 resident warps per SM are ever launched.
+#define DET_NV (RF_KT + 2)
+size_t det_warps() { return (size_t)64 * num_sms(); }
+size_t det_bytes() {
+    return align256(det_warps() * 2 * DET_NV * sizeof(double)) + align256(det_warps() * 2 * sizeof(int64_t));
 }
 
 struct Carved {
     double* recD;
     float2* recF;
+    double* part = nullptr;      // deterministic mode: [warps][2][DET_NV]
+    int64_t* wrow = nullptr;     // [warps][2]
 };
 
-lcdm_status carve(void* ws, size_t ws_bytes, int64_t B, Carved& c) {
-    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < ws_bytes_for(B)) return LCDM_ERR_WORKSPACE;
+lcdm_status carve(void* ws, size_t ws_bytes, int64_t B, Carved& c, int det = 0) {
+    if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < ws_bytes_for(B) + (det ? det_bytes() : 0))
+        return LCDM_ERR_WORKSPACE;
     c.recD = (double*)ws;
     c.recF = (float2*)((char*)ws + align256((size_t)B * NREC * sizeof(double)));
+    if (det) {
+        c.part = (double*)((char*)ws + ws_bytes_for(B));
+        c.wrow = (int64_t*)((char*)c.part + align256(det_warps() * 2 * DET_NV * sizeof(double)));
+    }
     return LCDM_OK;
 }
 
@@ -118,6 +136,9 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
     memset(&a, 0, sizeof(a));
     a.recD = cv.recD;
     a.recF = cv.recF;
+    a.part = cv.part;
+    a.wrow = cv.wrow;
+    a.det_cap = cv.part ? (int64_t)det_warps() : 0;
     a.status = status;
     a.offsets = offsets;
     a.z = z;
@@ -164,6 +185,32 @@ lcdm_status make_plan(const double* params, int64_t B, const int64_t* offsets, c
 }
 
 lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s);
+
+}  // namespace
+
+namespace lcdm {
+// The deterministic reduction's second pass: the shared rows' partial sums
+// added in warp order by one thread (a few thousand additions).
+__global__ void det_fixup_kernel(PairArgs a, int64_t nwarps) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int64_t w = 0; w < nwarps && w < a.det_cap; w++) {
+        for (int k = 0; k < 2; k++) {
+            const int64_t r = a.wrow[w * 2 + k];
+            if (r < 0 || (k == 1 && r == a.wrow[w * 2])) continue;
+            const double* v = a.part + (w * 2 + k) * DET_SLOT;
+            if (a.grad) for (int i = 0; i < a.ncol; i++) a.grad[r * a.ncol + i] += v[i];
+            if (a.loglike) a.loglike[r] += v[DET_SLOT - 1];
+        }
+    }
+}
+
+cudaError_t launch_det_fixup(const PairArgs& a, int64_t nwarps, cudaStream_t s) {
+    det_fixup_kernel<<<1, 32, 0, s>>>(a, nwarps);
+    return cudaGetLastError();
+}
+}  // namespace lcdm
+
+namespace {
 
 // The plan's launches: the value-only outputs of split_mask first (K = 0,
 // their tracks only, no reductions), then the tangent launch without them.
@@ -227,6 +274,12 @@ lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s
     if (P.npairs == 0) return LCDM_OK;
     cudaError_t e = t.launch[idx](P.args, (int)grid, block, s);
     g_launches++;
+    if (e != cudaSuccess) return LCDM_ERR_CUDA;
+    if (P.args.part && (P.args.grad || P.args.loglike)) {
+        // the shared rows' partial sums, added in warp order
+        e = launch_det_fixup(P.args, need_warps, s);
+        g_launches++;
+    }
     return e == cudaSuccess ? LCDM_OK : LCDM_ERR_CUDA;
 }
 
@@ -285,7 +338,7 @@ lcdm_status pairs_common(const double* params, int64_t B, const int64_t* offsets
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, status, opts);
     if (st != LCDM_OK) return st;
     Carved cv;
-    st = carve(ws, ws_bytes, B, cv);
+    st = carve(ws, ws_bytes, B, cv, opts->deterministic);
     if (st != LCDM_OK) return st;
     Plan P;
     st = make_plan(params, B, offsets, z, n, out, jac, cot, mobs, M, sigma, grad, loglike, status, opts, cv, P);
@@ -466,6 +519,7 @@ lcdm_status lcdm_distances_between(const double* params, int64_t B, const double
     if (between_npairs(B, n, opts, &npairs) != LCDM_OK || !z1 || (!out && !grad) || (grad && !cot))
         return LCDM_ERR_INVALID;
     if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // the row shift takes 4 or 5 columns
+    if (opts->deterministic && grad) return LCDM_ERR_UNSUPPORTED;
     lcdm_status st = check_pairs_args(params, B, offsets, z2, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
     const int ncol = opts->ncol;
@@ -531,6 +585,7 @@ lcdm_status lcdm_gauss_loglike_dz(const double* params, int64_t B, const int64_t
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
     if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // E(z) of the redshift kernel: 4 or 5 columns
+    if (opts->deterministic) return LCDM_ERR_UNSUPPORTED;
     size_t need = 0;
     lcdm_loglike_dz_workspace_size(B, n, opts, &need);
     if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return LCDM_ERR_WORKSPACE;
@@ -582,6 +637,7 @@ lcdm_status lcdm_distances_vjp_dz(const double* params, int64_t B, const int64_t
     lcdm_status st = check_pairs_args(params, B, offsets, z, n, cosmo_status, opts);
     if (st != LCDM_OK) return st;
     if (opts->ncol > 5) return LCDM_ERR_UNSUPPORTED;   // E(z) of the redshift kernel: 4 or 5 columns
+    if (opts->deterministic && grad) return LCDM_ERR_UNSUPPORTED;
     size_t need = 0;
     lcdm_loglike_dz_workspace_size(B, n, opts, &need);
     if (!ws || ((uintptr_t)ws & 255) != 0 || ws_bytes < need) return LCDM_ERR_WORKSPACE;
@@ -684,6 +740,7 @@ lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64
         (n > 0 && !z) || !cot || !grad || !cosmo_status || nchunks < 1 || nchunks > LCDM_HOST_MAX_CHUNKS)
         return LCDM_ERR_INVALID;
     if (offsets[0] != 0 || offsets[B] != n) return LCDM_ERR_INVALID;
+    if (opts->deterministic) return LCDM_ERR_UNSUPPORTED;
     for (int64_t r = 0; r < B; r++)
         if (offsets[r + 1] < offsets[r]) return LCDM_ERR_INVALID;
     const int ncol = opts->ncol;
@@ -763,7 +820,7 @@ lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64
 
 lcdm_status lcdm_workspace_size(int64_t B, const lcdm_opts* opts, size_t* bytes) {
     if (!opts_ok(opts) || B <= 0 || !bytes) return LCDM_ERR_INVALID;
-    *bytes = ws_bytes_for(B);
+    *bytes = ws_bytes_for(B) + (opts->deterministic ? det_bytes() : 0);
     return LCDM_OK;
 }
 
@@ -824,7 +881,7 @@ lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offset
     if (st != LCDM_OK) return st;
     if (!grad) cot = nullptr;   // forward-only shape
     Carved cv;
-    st = carve(ws, ws_bytes, B, cv);
+    st = carve(ws, ws_bytes, B, cv, opts->deterministic);
     if (st != LCDM_OK) return st;
     Plan P;
     st = make_plan(params, B, offsets, z, n, out, nullptr, cot, nullptr, 0, 1, grad, nullptr, cosmo_status, opts, cv,
@@ -841,7 +898,7 @@ lcdm_status lcdm_autotune(const double* params, int64_t B, const int64_t* offset
         if (opts->lane_map != LCDM_MAP_TUNED && map != opts->lane_map) continue;
         for (int block : blocks) {
             int occ = t.occ[idx](block);
-            for (int bps = 1; bps <= occ; bps *= 2) {
+            for (int bps = 1; bps <= occ; bps = (bps * 2 > occ && bps < occ) ? occ : bps * 2) {
                 float tot = 0;
                 for (int rep = 0; rep < 3; rep++) {
                     if (run_prep(params, B, opts, cv, cosmo_status, grad, nullptr, stream) != LCDM_OK)

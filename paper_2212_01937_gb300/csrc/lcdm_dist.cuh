@@ -154,17 +154,19 @@ LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h
 // Phi(w) = [R_C(1, 1-w) - (1-w)^-1/2] / w: the part of R_C(y + d, y) - y^-1/2
 // that is linear in w = d / (y + d), as a series for small w (coefficients
 // 1/(2n+1) - C(2n,n)/4^n, n >= 1) and directly otherwise.
+// The coefficients 1/(2n+1) - C(2n,n)/4^n, n = 1 .. 17 (exact rationals rounded).
+#define LCDM_PHI_CS {-0.16666666666666666, -0.175, -0.16964285714285715, -0.1623263888888889,                   \
+                     -0.1551846590909091, -0.14866286057692307, -0.14280598958333332, -0.13755708582261028,      \
+                     -0.13283900210731908, -0.1285780043829055, -0.12470983422320822, -0.12118025779724122,      \
+                     -0.1179439800756949, -0.11496322216658757, -0.11220638357823895, -0.10964690378838868,      \
+                     -0.10726233098788986}
 template <class S> LCDM_HD S phi_rc(const S& w, int* fail) {
     typedef typename Base<S>::type T;
-    const int NT = sizeof(T) == 4 ? 9 : 17;
-    if (sval(vof(w)) <= 0.1) {
-        double cs[17];
-        double bn = 1.0;
-        for (int n = 1; n <= NT; n++) {
-            bn *= (2.0 * n - 1.0) / (2.0 * n);
-            cs[n - 1] = 1.0 / (2.0 * n + 1.0) - bn;
-        }
+    constexpr int NT = sizeof(T) == 4 ? 9 : 17;
+    if (sval(vof(w)) <= cst<T>(0.1)) {
+        constexpr double cs[17] = LCDM_PHI_CS;
         S acc = w * cst<T>(0.0) + cst<T>(cs[NT - 1]);
+#pragma unroll
         for (int n = NT - 1; n >= 1; n--) acc = acc * w + cst<T>(cs[n - 1]);
         return acc;
     }

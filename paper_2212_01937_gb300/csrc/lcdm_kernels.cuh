@@ -53,11 +53,12 @@ template <class T> LCDM_HD void curv_map(T D, T Ok, T& S, T& SD, T& Sk) {
     T u = Ok * D * D;
     if (fabs(u) < (T)0.05) {
         // coefficients 1/(2n+1)!, 1/(2n)!
-        const double cs[8] = {1.0, 1.0 / 6, 1.0 / 120, 1.0 / 5040, 1.0 / 362880, 1.0 / 39916800,
-                              1.0 / 6227020800.0, 1.0 / 1307674368000.0};
-        const double cd2[8] = {1.0, 0.5, 1.0 / 24, 1.0 / 720, 1.0 / 40320, 1.0 / 3628800,
-                               1.0 / 479001600.0, 1.0 / 87178291200.0};
+        constexpr double cs[8] = {1.0, 1.0 / 6, 1.0 / 120, 1.0 / 5040, 1.0 / 362880, 1.0 / 39916800,
+                                  1.0 / 6227020800.0, 1.0 / 1307674368000.0};
+        constexpr double cd2[8] = {1.0, 0.5, 1.0 / 24, 1.0 / 720, 1.0 / 40320, 1.0 / 3628800,
+                                   1.0 / 479001600.0, 1.0 / 87178291200.0};
         T s = (T)cs[7], sd = (T)cd2[7], sk = (T)(7 * cs[7]);
+#pragma unroll
         for (int i = 6; i >= 0; i--) {
             s = (T)cs[i] + u * s;
             sd = (T)cd2[i] + u * sd;
@@ -102,7 +103,14 @@ struct PairArgs {
     int64_t chunk;           // pairs per warp (multiple of 32)
     int64_t base;            // CSR: index of the first pair (z, outputs and offsets are absolute)
     int interleave;          // lane l takes the l-th 32nd of the warp's range (else 32 consecutive pairs)
+    // deterministic reduction (optional): per warp, the partial sums of its
+    // first and last rows [warp][2][RF_KT + 2] and those rows [warp][2];
+    // rows owned by one warp are added directly (in program order)
+    double* part;
+    int64_t* wrow;
+    int64_t det_cap;         // warps with slots
 };
+enum { DET_SLOT = RF_KT + 2 };
 
 template <class T> struct IO;
 template <> struct IO<float> { typedef float type; };
@@ -259,7 +267,7 @@ LCDM_HD void eval_pair(typename std::conditional<PREC == 0, double, float>::type
     }
     // observables
     const TO z = zin;
-    const TO H0 = (TO)rd[RF_H0];
+    const TO H0 = recv<TO>(rd, rf, RF_H0);
     const TO DH = recv<TO>(rd, rf, RF_DH), tH = recv<TO>(rd, rf, RF_TH), Ok = recv<TO>(rd, rf, RF_OK);
     TO S, SD, Sk;
     curv_map<TO>(Ichi, Ok, S, SD, Sk);
@@ -312,22 +320,41 @@ __device__ __forceinline__ int64_t row_search(const int64_t* __restrict__ off, i
     return lo;
 }
 
+// Row of an absolute pair index.
+__device__ __forceinline__ int64_t row_of(const PairArgs& a, int64_t p) {
+    return a.layout == LAYOUT_CSR ? row_search(a.offsets, a.B, p) : p / a.nrow;
+}
+
+// Add one row's sums v[] (ncol gradient entries, then the log-likelihood at
+// index nll) from one lane: into the warp's own slot when the row is the
+// warp's first or last row and the reduction is deterministic, else into the
+// row's FP64 sums.
+__device__ __forceinline__ void add_row(const PairArgs& a, int64_t row, const double* v, int nll, int64_t warp,
+                                        int64_t wf, int64_t wl) {
+    if (a.part && warp < a.det_cap && (row == wf || row == wl)) {
+        double* slot = a.part + (warp * 2 + (row == wf ? 0 : 1)) * DET_SLOT;
+        if (a.grad) for (int i = 0; i < a.ncol; i++) atomicAdd(slot + i, v[i]);
+        if (a.loglike) atomicAdd(slot + DET_SLOT - 1, v[nll]);
+        return;
+    }
+    if (a.grad) for (int i = 0; i < a.ncol; i++) atomicAdd(a.grad + row * a.ncol + i, v[i]);
+    if (a.loglike) atomicAdd(a.loglike + row, v[nll]);
+}
+
 __device__ __forceinline__ double acc_to_double(double v) { return v; }
 __device__ __forceinline__ double acc_to_double(df64 v) { return (double)v.hi + (double)v.lo; }
 
 // Warp sum of the per-lane accumulators of one row, added to the row's FP64 sums.
 template <int NV, int K, class AccT>
-__device__ __forceinline__ void flush_row(const AccT* acc, int64_t row, const PairArgs& a, int lane) {
+__device__ __forceinline__ void flush_row(const AccT* acc, int64_t row, const PairArgs& a, int lane, int64_t warp,
+                                          int64_t wf, int64_t wl) {
     double v[NV];
 #pragma unroll
     for (int i = 0; i < NV; i++) {
         v[i] = acc_to_double(acc[i]);
         for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
     }
-    if (lane == 0) {
-        if (a.grad) for (int i = 0; i < a.ncol; i++) atomicAdd(a.grad + row * a.ncol + i, v[i]);
-        if (a.loglike) atomicAdd(a.loglike + row, v[K + 1]);
-    }
+    if (lane == 0) add_row(a, row, v, K + 1, warp, wf, wl);
 }
 
 template <int PREC, int K, bool WT, bool WX>
@@ -342,12 +369,25 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
     const bool loglike = a.mobs != nullptr;
     const TO inv_sig = (TO)(1.0 / a.sigma);
     const TO lnorm = (TO)(-log(a.sigma * 2.5066282746310002));
+    const TO Mobs = (TO)a.M;
     typedef typename std::conditional<PREC == 0, double, df64>::type AccT;
     int64_t row = -1;
     AccT acc[NV];
     int64_t acc_row = -1;
 #pragma unroll
     for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
+    // deterministic reduction: the warp's first and last rows, its slots zeroed
+    int64_t wf = -1, wl = -1;
+    if (a.part && reduce && warp < a.det_cap) {
+        if (start < end) {
+            wf = row_of(a, a.base + start);
+            wl = row_of(a, a.base + end - 1);
+        }
+        if (lane < 2 * DET_SLOT) a.part[warp * 2 * DET_SLOT + lane] = 0.0;
+        if (lane < 2) a.wrow[warp * 2 + lane] = lane == 0 ? wf : wl;
+        __syncwarp();
+        __threadfence_block();
+    }
     const int64_t len = end - start, nb = (len + 31) / 32, nb_all = a.chunk / 32;
     const int64_t s_lane = a.interleave ? nb : 1, s_it = a.interleave ? 1 : 32;
     // With a full-SM block (256 threads, one block per SM) the warps step through
@@ -414,7 +454,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
         for (int i = 0; i < NV; i++) c[i] = 0;
         if (active && st == ST_OK && !fail) {
             if (loglike) {
-                TO r = (load_io<TO>(a.mobs, zi) - o.v[O_MU] - (TO)a.M) * inv_sig;
+                TO r = (load_io<TO>(a.mobs, zi) - o.v[O_MU] - Mobs) * inv_sig;
                 TO w = r * inv_sig;
                 c[0] = w * o.h0[O_MU];
 #pragma unroll
@@ -439,7 +479,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
             for (int i = 0; i < NV; i++) acc[i] = acc[i] + c[i];
             continue;
         }
-        if (acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane);
+        if (acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane, warp, wf, wl);
         if (uniform) {
 #pragma unroll
             for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0) + c[i];
@@ -448,16 +488,13 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
             double cd_[NV];
 #pragma unroll
             for (int i = 0; i < NV; i++) cd_[i] = (double)c[i];
-            if (seg_reduce<NV>(cd_, row) && active) {
-                if (a.grad) for (int i = 0; i < a.ncol; i++) atomicAdd(a.grad + row * a.ncol + i, cd_[i]);
-                if (a.loglike) atomicAdd(a.loglike + row, cd_[K + 1]);
-            }
+            if (seg_reduce<NV>(cd_, row) && active) add_row(a, row, cd_, K + 1, warp, wf, wl);
 #pragma unroll
             for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
             acc_row = -1;
         }
     }
-    if (reduce && acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane);
+    if (reduce && acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane, warp, wf, wl);
 }
 
 }  // namespace lcdm

@@ -48,6 +48,8 @@ PairsTable table_mix_k0();
 PairsTable table_mix_k3();
 PairsTable table_mix_k4();
 PairsTable table_f64_k6();
+// second pass of the deterministic reduction (defined with the other kernels)
+cudaError_t launch_det_fixup(const PairArgs& a, int64_t nwarps, cudaStream_t s);
 PairsTable table_mix_k6();
 
 }  // namespace lcdm

@@ -24,7 +24,8 @@ _lib = None
 
 class Opts(ctypes.Structure):
     _fields_ = [("ncol", ctypes.c_int32), ("precision", ctypes.c_int32), ("layout", ctypes.c_int32),
-                ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("lane_map", ctypes.c_int32)]
+                ("block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32), ("lane_map", ctypes.c_int32),
+                ("deterministic", ctypes.c_int32)]
 
 
 LANE_MAP = {"tuned": 0, "contiguous": 1, "interleaved": 2}
@@ -126,7 +127,7 @@ class Call:
     """Prepared arguments of one batch (validated and placed on the device)."""
 
     def __init__(self, params, z, offsets=None, layout=None, precision="fp32", block=0, blocks_per_sm=0,
-                 workspace=None, lane_map="tuned"):
+                 workspace=None, lane_map="tuned", deterministic=False):
         lib = load()
         if not params.is_cuda:
             raise ValueError("params must be a CUDA tensor")
@@ -154,7 +155,8 @@ class Call:
         else:
             self.n = self.z.numel()
             self.npairs = self.B * self.n
-        self.opts = Opts(ncol, PRECISION[precision], LAYOUT[layout], block, blocks_per_sm, LANE_MAP[lane_map])
+        self.opts = Opts(ncol, PRECISION[precision], LAYOUT[layout], block, blocks_per_sm, LANE_MAP[lane_map],
+                         1 if deterministic else 0)
         nbytes = ctypes.c_size_t()
         _check(lib.lcdm_workspace_size(self.B, ctypes.byref(self.opts), ctypes.byref(nbytes)))
         if workspace is not None and workspace.numel() >= nbytes.value:

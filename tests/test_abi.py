@@ -119,3 +119,27 @@ def test_seven_column_rows_refused_where_unsupported(cdll):
                                       big, None) == 4
     assert cdll.lcdm_distances_vjp_dz(fake, i64(4), fake, fake, i64(8), six(), none6, None, fake, fake,
                                       ctypes.byref(o7), ws, big, None) == 4
+
+
+def test_deterministic_workspace_and_refusals(cdll):
+    """The deterministic reduction needs a larger workspace; the entry points
+    that do not offer it refuse it before any CUDA call."""
+    from paper_2212_01937_gb300.lcdm import Opts
+    vp, i64, sz = ctypes.c_void_p, ctypes.c_int64, ctypes.c_size_t
+    n0, n1 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert cdll.lcdm_workspace_size(i64(64), ctypes.byref(Opts(4, 1, 0, 0, 0, 0, 0)), ctypes.byref(n0)) == 0
+    od = Opts(4, 1, 0, 0, 0, 0, 1)
+    assert cdll.lcdm_workspace_size(i64(64), ctypes.byref(od), ctypes.byref(n1)) == 0
+    assert n1.value > n0.value
+    assert cdll.lcdm_workspace_size(i64(64), ctypes.byref(Opts(4, 1, 0, 0, 0, 0, 2)), ctypes.byref(n1)) == 1
+    fake, ws, big = vp(0x1000), vp(0x100000), sz(1 << 40)
+    six = lambda: (ctypes.c_void_p * 6)(*([0x1000] * 6))
+    none6 = (ctypes.c_void_p * 6)()
+    assert cdll.lcdm_gauss_loglike_dz(fake, i64(4), fake, fake, fake, i64(8), ctypes.c_double(0.0),
+                                      ctypes.c_double(0.1), fake, None, fake, None, fake, ctypes.byref(od), ws,
+                                      big, None) == 4
+    assert cdll.lcdm_distances_between(fake, i64(4), fake, fake, fake, i64(8), six(), six(), fake, fake,
+                                       ctypes.byref(od), ws, big, None) == 4
+    offs = (ctypes.c_int64 * 5)(0, 2, 4, 6, 8)
+    assert cdll.lcdm_distances_vjp_host(fake, i64(4), offs, fake, i64(8), six(), none6, fake, fake,
+                                        ctypes.byref(od), ws, big, ctypes.c_int32(2), None) == 4
