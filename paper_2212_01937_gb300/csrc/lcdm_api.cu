@@ -720,8 +720,10 @@ lcdm_status lcdm_distances_static(const double* params, int64_t B, const int64_t
     void* ws = nullptr;
     st = static_workspace(&ws);
     if (st != LCDM_OK) return st;
+    lcdm_opts o = *opts;
+    o.deterministic = 0;   // forward values only: there is no reduction
     return pairs_common(params, B, offsets, z, n, out, nullptr, nullptr, nullptr, 0, 1, nullptr, nullptr,
-                        cosmo_status, opts, ws, LCDM_STATIC_WS_BYTES, stream);
+                        cosmo_status, &o, ws, LCDM_STATIC_WS_BYTES, stream);
 }
 
 
