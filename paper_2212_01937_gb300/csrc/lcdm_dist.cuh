@@ -27,54 +27,57 @@ template <class T> LCDM_HD T rc_any(T x, T y, int* fail) {
     return rc_value(x, y, fail);
 }
 
-// The R_J tracks are given by h_j = p_j - x1 (their distance from the single
-// argument): the callers form h_j directly, without cancellation.  NEED_RD1:
-// return R_D(x2, x3, x1); WANT_DJ: return DJ = (R_J(last track) - R_D1) / h.
+// The triple enters through square roots: x1 = u1^2 and the pair y = u^2
+// (a conjugate pair, or two reals).  The R_J tracks are given by
+// h_j = p_j - x1 (their distance from the single argument): the callers form
+// h_j directly, without cancellation.  NEED_RD1: return R_D(y_a, y_b, x1);
+// WANT_DJ: return DJ = (R_J(last track) - R_D1) / h.  Written once for plain
+// and dual numbers: tangents are carried through the duplication sequence
+// itself (see carlson_sym; the note below on why not by (2.10)-(2.12)).
 template <int NJ, bool NEED_RD1, bool WANT_DJ, class T, class PT>
-LCDM_HD void carlson_any(T x1, PT pr, const T* h, T& RF, T& RD1, T* RJ, int* fail, T* DJ = 0) {
-    T tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1], hh[NJ > 0 ? NJ : 1];
+LCDM_HD void carlson_any(const T& u1, const PT& up, const T* h, T& RF, T& RD1, T* RJ, int* fail, T* DJ = 0) {
+    const T x1 = u1 * u1;
+    const PT pr = up * up;
+    T tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1], hh[NJ > 0 ? NJ : 1], dl[NJ > 0 ? NJ : 1];
     bool pv[NJ > 0 ? NJ : 1];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
         T p = x1 + h[j];
-        pv[j] = sval(p) < 0;
+        pv[j] = sval(vof(p)) < 0;
         if (pv[j]) {
             q[j] = -p;
             s[j] = (x1 * (psum(pr) + q[j]) - pprod(pr)) / (x1 + q[j]);
-            if (!(sval(s[j]) > 0)) *fail = 2;
+            if (!(sval(vof(s[j])) > 0)) *fail = 2;
             tr[j] = s[j];
             hh[j] = s[j] - x1;
         } else {
             tr[j] = p;
             hh[j] = h[j];
         }
+        // (p - x1)(p - y_a)(p - y_b) from the members: |p - y|^2 has no cancellation
+        dl[j] = hh[j] * pprod(prsub(tr[j], pr));
     }
-    if constexpr (WANT_DJ && NJ > 0) {
-        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, true, false>(x1, pr, tr, fail, hh[NJ - 1]);
-        RF = R.RF; RD1 = R.RD1;
-#pragma unroll
-        for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
-        *DJ = R.DJ;
-    } else if constexpr (NEED_RD1) {
-        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, true, PT, false, false>(x1, pr, tr, fail);
-        RF = R.RF; RD1 = R.RD1;
-#pragma unroll
-        for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
-    } else {
-        DupResult<T, NJ, PT> R = carlson_dup<T, NJ, false>(x1, pr, tr, fail);
-        RF = R.RF; RD1 = RF;
-#pragma unroll
-        for (int j = 0; j < NJ; j++) RJ[j] = R.RJ[j];
-    }
+    constexpr int JL = NJ > 0 ? NJ - 1 : 0;
+    const T PiL = WANT_DJ ? pprod(prsub(tr[JL], pr)) : x1;
+    SymResult<T, NJ> R = carlson_sym<T, NJ, NEED_RD1 || WANT_DJ, WANT_DJ>(
+        sabs(u1), proot_sum(up), proot_prod(up), pis_cplx(up), tr, dl, fail, hh[JL], PiL);
+    RF = R.RF;
+    RD1 = R.RD1;
+    // principal values (the tracks ran at s_j)
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        if (pv[j]) {
+        if (!pv[j]) {
+            RJ[j] = R.RJ[j];
+        } else {
             T xy = pprod(pr), sq = s[j] * q[j];
-            T rc = rc_value(xy + sq, sq, fail);
-            RJ[j] = ((s[j] - x1) * RJ[j] - cst<T>(3.0) * RF + cst<T>(3.0) * ssqrt(x1 * xy / (xy + sq)) * rc)
-                    / (q[j] + x1);
-            if (WANT_DJ && j == NJ - 1) *DJ = (RJ[j] - RD1) / h[j];
+            T rc = rc_any(xy + sq, sq, fail);
+            RJ[j] = ((s[j] - x1) * R.RJ[j] - RF * cst<typename Base<T>::type>(3.0)
+                     + ssqrt(x1 * xy / (xy + sq)) * rc * cst<typename Base<T>::type>(3.0)) / (q[j] + x1);
         }
+    }
+    if constexpr (WANT_DJ && NJ > 0) {
+        *DJ = R.DJ;
+        if (pv[JL]) *DJ = (RJ[JL] - RD1) / h[JL];
     }
 }
 
@@ -107,50 +110,6 @@ template <class T, int K> LCDM_HD Dual<T, K> rc_any(const Dual<T, K>& x, const D
 // near-double root at rho = 0) and d X / d Omega_r0 at 3e-5 for
 // Omega_r0 = 1e-12, where the dual tangents give 5e-14 and 4e-13.  Only
 // R_C's tangents use (2.10) (R_C(x, y) = R_F(x, y, y), no differences).
-template <int NJ, bool NEED_RD1, bool WANT_DJ, class T, int K, class PD>
-LCDM_HD void carlson_any(const Dual<T, K>& x1, const PD& pr, const Dual<T, K>* h, Dual<T, K>& RF,
-                         Dual<T, K>& RD1, Dual<T, K>* RJ, int* fail, Dual<T, K>* DJ = 0) {
-    typedef Dual<T, K> D;
-    D tr[NJ > 0 ? NJ : 1], s[NJ > 0 ? NJ : 1], q[NJ > 0 ? NJ : 1], hh[NJ > 0 ? NJ : 1];
-    bool pv[NJ > 0 ? NJ : 1];
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-        D p = x1 + h[j];
-        pv[j] = sval(p.v) < 0;
-        if (pv[j]) {
-            q[j] = -p;
-            s[j] = (x1 * (psum(pr) + q[j]) - pprod(pr)) / (x1 + q[j]);
-            if (!(sval(s[j].v) > 0)) *fail = 2;
-            tr[j] = s[j];
-            hh[j] = s[j] - x1;
-        } else {
-            tr[j] = p;
-            hh[j] = h[j];
-        }
-    }
-    D Jd[NJ > 0 ? NJ : 1];
-    DupResult<D, NJ, PD> R = carlson_dup<D, NJ, NEED_RD1 || WANT_DJ, PD, WANT_DJ, false>(
-        x1, pr, tr, fail, hh[NJ > 0 ? NJ - 1 : 0]);
-    RF = R.RF;
-    RD1 = R.RD1;
-#pragma unroll
-    for (int j = 0; j < NJ; j++) Jd[j] = R.RJ[j];
-    if constexpr (WANT_DJ) *DJ = R.DJ;
-    // principal values (the tracks ran at s_j) and the divided difference fallback
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-        if (!pv[j]) {
-            RJ[j] = Jd[j];
-        } else {
-            D xy = pprod(pr), sq = s[j] * q[j];
-            D rc = rc_dual_pos(xy + sq, sq, fail);
-            RJ[j] = ((s[j] - x1) * Jd[j] - RF * cst<T>(3.0) + ssqrt(x1 * xy / (xy + sq)) * rc * cst<T>(3.0))
-                    / (q[j] + x1);
-        }
-    }
-    if (WANT_DJ && NJ > 0 && pv[NJ > 0 ? NJ - 1 : 0]) *DJ = (RJ[NJ - 1] - RD1) / h[NJ - 1];
-}
-
 // Phi(w) = [R_C(1, 1-w) - (1-w)^-1/2] / w: the part of R_C(y + d, y) - y^-1/2
 // that is linear in w = d / (y + d), as a series for small w (coefficients
 // 1/(2n+1) - C(2n,n)/4^n, n >= 1) and directly otherwise.
@@ -208,7 +167,6 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     S uAB = nrm * (nA * nB + pprod(nP));
     PS uAP = pscale(pscale(nP, nA) + pscale(pswap(nP), nB), nrm);
     S x1 = uAB * uAB;
-    PS pr = uAP * uAP;
     S rhoB = B + one;
     PS rhoP = padd(P, one);
     S ppPA = pprod(padd(pscale(rhoP, epsA), one));     // |P - A|^2 / rho_A^2
@@ -218,10 +176,10 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
     int jt = 0, jx = WT ? 1 : 0;
     if (WT) p[jt] = -(mA * ppPA * rhoB * z2);          // lam u_A5^2 - x1
     if (WX) p[jx] = -(lam * ppPB * z2);                // lam u_B0^2 - x1
-    S RF, RD1, RJ[NJ > 0 ? NJ : 1], DJ;
-    carlson_any<NJ, WX, WX>(x1, pr, p, RF, RD1, RJ, fail, &DJ);
-    Ichi = RF * (z + z);                               // eq. (3.7)
-    if (WT) {                                          // eq. (3.8), i = A
+    // eq. (3.8), i = A: everything but the R_F and R_J terms before the
+    // duplication sequence, so that only three factors stay live across it
+    S RCp, kB, cJ;
+    if (WT) {
         // R_C(s_A5^2, q_A5^2) scaled by eps_A (homogeneity) is R_C(k s5, k q5) =
         // k^-1/2 R_C(s5, q5) with k = (1+z) / cA, cA = (1 + eps_A)(1 + eps_A (1+z)).
         // The part of k^-1/2 linear in eps_A is combined with -eps_A R_F: the two
@@ -233,9 +191,16 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
         S cA = (one + epsA) * (one + epsA * (one + z));
         S q5 = x1 + p[jt];
         S s5 = q5 + mA * pprod(rhoP) * rhoB * z2 * cA * (izh * izh);
-        S RCp = rc_any(s5, q5, fail) * izh;
-        S Bk = RCp * ((cst<T>(2.0) + z + epsA * (one + z)) / (ssqrt(cA) + one)) - RF;
-        It = (RCp + epsA * Bk - mA * (one + epsA * rhoB) * ppPA * RJ[jt] * (z2 * third)) * (z + z);
+        RCp = rc_any(s5, q5, fail) * izh;
+        kB = (cst<T>(2.0) + z + epsA * (one + z)) / (ssqrt(cA) + one);
+        cJ = mA * (one + epsA * rhoB) * ppPA * (z2 * third);
+    }
+    S RF, RD1, RJ[NJ > 0 ? NJ : 1], DJ;
+    carlson_any<NJ, WX, WX>(uAB, uAP, p, RF, RD1, RJ, fail, &DJ);
+    Ichi = RF * (z + z);                               // eq. (3.7)
+    if (WT) {
+        S Bk = RCp * kB - RF;
+        It = (RCp + epsA * Bk - cJ * RJ[jt]) * (z + z);
     }
     if (WX) {                                          // eq. (3.9), i = B, l = A
         // The l = A part of (3.9), rho_A G, is a sum of O(1) terms that cancel to
@@ -288,19 +253,20 @@ LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, 
     S uA = nrm * (nA + pprod(nP));
     PS uP = pscale(nP + pscale(pswap(nP), nA), nrm);
     S x1 = uA * uA;
-    PS pr = uP * uP;
     enum { NJ = WT ? 1 : 0 };
     S p[1];
     S rhoA = A + one;
     if (WT) p[0] = rhoA * z2;                          // u_A5^2 - x1
-    S RF, RD1, RJ[1];
-    carlson_any<NJ, WX, false>(x1, pr, p, RF, RD1, RJ, fail);
-    Ichi = amh * RF * (z + z);                         // eq. (B.1)
-    if (WT) {                                          // eq. (B.2)
+    S RC5;                                             // eq. (B.2)'s R_C term, before the duplication
+    if (WT) {
         S s5 = YA * ppYP * (one + z) + XA * ppXP;
         S q5 = (x1 + p[0]) * (one + z);
-        It = amh * (z + z) * (RJ[0] * (z2 * cst<T>(1.0 / 3.0)) + rc_any(s5 * s5, q5, fail));
+        RC5 = rc_any(s5 * s5, q5, fail);
     }
+    S RF, RD1, RJ[1];
+    carlson_any<NJ, WX, false>(uA, uP, p, RF, RD1, RJ, fail);
+    Ichi = amh * RF * (z + z);                         // eq. (B.1)
+    if (WT) It = amh * (z + z) * (RJ[0] * (z2 * cst<T>(1.0 / 3.0)) + RC5);   // eq. (B.2)
     if (WX) {                                          // eq. (B.3), i = A
         S ppPA = pprod(padd(P, -A));
         S eA = one / (XA + YA);
@@ -332,14 +298,13 @@ LCDM_NI void quartic_limits(const S& mA, const S& epsA, const S& B, const PS& P,
     S uAB = nrm * (nA * nB + pprod(nP));
     PS uAP = pscale(pscale(nP, nA) + pscale(pswap(nP), nB), nrm);
     S x1 = uAB * uAB;
-    PS pr = uAP * uAP;
     S rhoB = B + one;
     PS rhoP = padd(P, one);
     S ppPA = pprod(padd(pscale(rhoP, epsA), one));
     S p[1];
     p[0] = -(mA * ppPA * rhoB);
     S RF, RD1, RJ[1];
-    carlson_any<1, false, false>(x1, pr, p, RF, RD1, RJ, fail);
+    carlson_any<1, false, false>(uAB, uAP, p, RF, RD1, RJ, fail);
     Ichi = RF * cst<T>(2.0);                                   // eq. (3.7), z -> inf
     S kq5 = (x1 + p[0]) / ((one + epsA) * epsA);
     S ks5 = kq5 + mA * pprod(rhoP) * rhoB;
@@ -357,12 +322,10 @@ LCDM_NI void cubic_limits(const S& A, const S& amh, const S& qA, const PS& qP, c
     // u_A / z -> N n_P n_P*,  u_P / z -> N n_P* n_A  (the plain u_i -> Y_i = sqrt(-r_i))
     S uA = nrm * pprod(nP);
     PS uP = pscale(pswap(nP), nA * nrm);
-    S x1 = uA * uA;
-    PS pr = uP * uP;
     S p[1];
     p[0] = A + one;                                            // u_A5^2 - u_A^2 = rho_A
     S RF, RD1, RJ[1];
-    carlson_any<1, false, false>(x1, pr, p, RF, RD1, RJ, fail);
+    carlson_any<1, false, false>(uA, uP, p, RF, RD1, RJ, fail);
     Ichi = amh * RF * cst<T>(2.0);                             // eq. (B.1), z -> inf
     It = amh * RJ[0] * cst<T>(2.0 / 3.0);                      // eq. (B.2), z -> inf
 }

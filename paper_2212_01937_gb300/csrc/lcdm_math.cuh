@@ -608,4 +608,189 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
     return R;
 }
 
+// ---------------------------------------------------------------------------
+// The same duplication sequence for R_F(x1, y_a, y_b), R_D(y_a, y_b, x1) and
+// NJ R_J(x1, y_a, y_b, p_j) (and the divided-difference track), all symmetric
+// in the pair (y_a, y_b), carried on real numbers only: the pair enters
+// through sigma = y_a + y_b and pi = y_a y_b, and its square roots through
+// S = s_a + s_b and P = s_a s_b (real for a conjugate pair as for two reals).
+// One step, with s1 = sqrt(x1), lambda = s1 S + P:
+//   x1 + lambda = (s1 + s_a)(s1 + s_b) = s1^2 + s1 S + P,
+//   sigma' = S (S + 2 s1) / 4,   pi' = x1' S^2 / 4,   x1' = (x1 + lambda) / 4
+// (y_a + lambda = (s_a + s1)(s_a + s_b)): sums and products of non-negative
+// numbers, so no step cancels, not even for a pair near the negative real
+// axis.  The square roots of the starting triple are given (u1 and the pair
+// u of the callers, x1 = u1^2, y = u^2), so the first step takes none; after
+// it the pair lies in the right half-plane and P = sqrt(pi),
+// S = sqrt(sigma + 2P) add positive numbers.  For the stopping rule the
+// pair's distance from the mean mu follows from
+//   (y_a - mu)(y_b - mu) = pi - mu sigma + mu^2   (|y - mu|^2 for a conjugate pair),
+//   (y_a - mu)^2 + (y_b - mu)^2 = (sigma - 2 mu)^2 - 2 (pi - mu sigma + mu^2)   (two reals).
+// The caller gives, per track, delta_j = (p_j - x1)(p_j - y_a)(p_j - y_b)
+// (formed from the members, where it does not cancel) and, for the
+// divided-difference track, hl = p_last - x1 and PiL = (p_last - y_a)(p_last - y_b).
+// ---------------------------------------------------------------------------
+template <class T, int NJ>
+struct SymResult {
+    T RF;      // R_F(x1, y_a, y_b)
+    T RD1;     // R_D(y_a, y_b, x1)
+    T RJ[NJ > 0 ? NJ : 1];
+    T DJ;      // (R_J(last track) - R_D1) / hl   (DDL)
+};
+
+template <class T, int NJ, bool WANT_D, bool DDL = false>
+LCDM_NI SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, const T* dj, int* fail, T hl = T(),
+                                     T PiL = T()) {
+    static_assert(!DDL || (WANT_D && NJ > 0), "the divided-difference track needs R_D and an R_J track");
+    SymResult<T, NJ> R;
+    float mag = fabsf((float)sval(s1));
+    mag = mag * mag;
+    {
+        const float a = fabsf((float)sval(S)), b = fabsf((float)sval(P));
+        if (a * a > mag) mag = a * a;
+        if (b > mag) mag = b;
+    }
+    T p[NJ > 0 ? NJ : 1], delta[NJ > 0 ? NJ : 1], sJ[NJ > 0 ? NJ : 1];
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        p[j] = pj[j];
+        const float a = fabsf((float)sval(p[j]));
+        if (a > mag) mag = a;
+    }
+    // scale by 2^-e, e even: x, y, p by 2^-e, square roots by 2^-e/2
+    const int e = even_exponent(mag);
+    s1 = sldexp(s1, -e / 2);
+    S = sldexp(S, -e / 2);
+    P = sldexp(P, -e);
+    T x1 = s1 * s1;
+    T sig = S * S - cst<T>(2.0) * P;   // exact enough for the first stopping test (see above)
+    T pi = P * P;
+#pragma unroll
+    for (int j = 0; j < NJ; j++) {
+        p[j] = sldexp(p[j], -e);
+        delta[j] = sldexp(dj[j], -3 * e);
+        sJ[j] = cst<T>(0.0);
+    }
+    T sD1 = cst<T>(0.0);
+    T f = cst<T>(1.0);
+    T hs = cst<T>(0.0), sDD = cst<T>(0.0);
+    if (DDL) {
+        hs = sldexp(hl, -e);
+        PiL = sldexp(PiL, -2 * e);
+    }
+    const T tol = Prec<T>::tol();
+    int m = 0;
+#pragma unroll 1
+    for (; m < Prec<T>::maxit; m++) {
+        T mu = x1 + sig;
+#pragma unroll
+        for (int j = 0; j < NJ; j++) mu = mu + p[j];
+        mu = mu * cst<T>(1.0 / (3 + NJ));
+        T lim = tol * mu;
+        T lim2 = lim * lim;
+        T dx = x1 - mu;
+        T v = pi - mu * sig + mu * mu;
+        T u = sig - cst<T>(2.0) * mu;
+        T dev2 = cplx ? v : u * u - cst<T>(2.0) * v;
+        bool conv = sval(dx * dx) <= sval(lim2) && sval(dev2) <= sval(lim2);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            T dp = p[j] - mu;
+            conv = conv && sval(dp * dp) <= sval(lim2);
+        }
+        if (conv) break;
+        if (m > 0) {
+            s1 = ssqrt(x1);
+            P = ssqrt(pi);
+            S = ssqrt(sig + cst<T>(2.0) * P);
+        }
+        T lam = s1 * S + P;
+        T xl = x1 + lam;                       // (s1 + s_a)(s1 + s_b)
+        if (WANT_D) sD1 = sD1 + f / (s1 * xl);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) {
+            T sq = ssqrt(p[j]);
+            T g = p[j] + sq * S + P;           // (sq + s_a)(sq + s_b)
+            T d = (sq + s1) * g;
+            T f3 = f * f * f;
+            T ee = f3 * delta[j] / (d * d);
+            if (!(DDL && j == NJ - 1)) sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
+            if (DDL && j == NJ - 1) {
+                // as in carlson_dup, with g(b) = x1 + lambda and g(a) = g
+                T eh = f3 * PiL / (d * d);
+                T F1 = rc1_minus1_over_e(ee, fail);
+                T dx1 = cst<T>(2.0) * s1 * xl;
+                T ddp = f * (g + cst<T>(2.0) * s1 * (sq + s1 + S)) / (sq + s1);
+                sDD = sDD + f * (eh * F1 / d - ddp / (d * dx1));
+            }
+        }
+        x1 = xl * cst<T>(0.25);
+        sig = S * (S + cst<T>(2.0) * s1) * cst<T>(0.25);
+        pi = x1 * (S * S) * cst<T>(0.25);
+#pragma unroll
+        for (int j = 0; j < NJ; j++) p[j] = (p[j] + lam) * cst<T>(0.25);
+        f = f * cst<T>(0.25);
+    }
+    if (m == Prec<T>::maxit) *fail = 1;
+    // R_F series: Y_a + Y_b = (2A - sigma)/A, Y_a Y_b = (A^2 - A sigma + pi)/A^2
+    {
+        T A = (x1 + sig) * cst<T>(1.0 / 3.0), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA;
+        T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
+        T e2 = X * sY + pY, e3 = X * pY;
+        T ser = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
+                - e2 * e3 * cst<T>(3.0 / 44.0);
+        R.RF = sldexp(ser / ssqrt(A), -e / 2);
+    }
+    if (WANT_D) {
+        T A = (sig + cst<T>(3.0) * x1) * cst<T>(0.2), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA;
+        T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
+        T ser = rj_series<T, T>(X, sY, pY, X);
+        R.RD1 = sldexp(f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1, -3 * e / 2);
+    } else {
+        R.RD1 = R.RF;
+    }
+#pragma unroll
+    for (int j = 0; j < (DDL ? NJ - 1 : NJ); j++) {
+        T A = (x1 + sig + cst<T>(2.0) * p[j]) * cst<T>(0.2), iA = cst<T>(1.0) / A;
+        T X = (A - x1) * iA, Pp = (A - p[j]) * iA;
+        T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
+        T ser = rj_series<T, T>(X, sY, pY, Pp);
+        R.RJ[j] = sldexp(f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j], -3 * e / 2);
+    }
+    R.DJ = R.RD1;
+    if (DDL) {
+        // the final series' divided difference, as in carlson_dup
+        const T sgm = x1 + sig;
+        const T u1 = x1 + hs * f;
+        T A1 = (sgm + cst<T>(2.0) * u1) * cst<T>(0.2), A2 = (sgm + cst<T>(2.0) * x1) * cst<T>(0.2);
+        T iA1 = cst<T>(1.0) / A1, iA2 = cst<T>(1.0) / A2;
+        T dInv = cst<T>(-0.4) * iA1 * iA2;
+        DD<T> inv = mkdd<T>(iA1, iA2, dInv);
+        DD<T> X = cst<T>(1.0) - inv * x1;
+        DD<T> sY = cst<T>(2.0) - inv * sig;
+        DD<T> inv2 = inv * inv;
+        DD<T> pY = (cst<T>(1.0) - inv * sig) + inv2 * pi;
+        DD<T> Pq = mkdd<T>(cst<T>(1.0) - u1 * iA1, cst<T>(1.0) - x1 * iA2, sgm * cst<T>(-0.2) * iA1 * iA2);
+        DD<T> ser = rj_series<DD<T>, T>(X, sY, pY, Pq);
+        T r1 = ssqrt(A1), r2 = ssqrt(A2);
+        T a32_1 = iA1 / r1, a32_2 = iA2 / r2;
+        T dA32 = cst<T>(-0.4) * (A1 + r1 * r2 + A2) / (r1 + r2) * a32_1 * a32_2;
+        T dser = dA32 * ser.v1 + a32_2 * ser.d;
+        R.DJ = sldexp(f * f * dser + cst<T>(6.0) * sDD, -5 * e / 2);
+        R.RJ[NJ - 1] = R.RD1 + hl * R.DJ;
+    }
+    return R;
+}
+
+// Square roots' sum S and product P of the pair whose members are the squares
+// of u (the callers' u's: y = u^2, principal roots |u| resp. +-u with Re >= 0).
+template <class S> LCDM_HD S proot_sum(const CPair<S>& u) { return sabs(u.c.re) * cst_like(u.c.re, 2.0); }
+template <class S> LCDM_HD S proot_sum(const RPair<S>& u) { return sabs(u.a) + sabs(u.b); }
+template <class S> LCDM_HD S proot_prod(const CPair<S>& u) { return norm2(u.c); }
+template <class S> LCDM_HD S proot_prod(const RPair<S>& u) { return sabs(u.a * u.b); }
+template <class S> LCDM_HD bool pis_cplx(const CPair<S>&) { return true; }
+template <class S> LCDM_HD bool pis_cplx(const RPair<S>&) { return false; }
+
 }  // namespace lcdm
