@@ -315,11 +315,15 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
         }
     }
     // Newton polishing on the original coefficients (the monic ones carry the
-    // rounding of the division by alpha_n), evaluated by the compensated scheme
+    // rounding of the division by alpha_n), evaluated by the compensated
+    // scheme, each root by the lane that owns it.  A root whose imaginary part
+    // is negligible (|Im| <= 1e-12 |z|: the classification's test) is put on
+    // the real axis first and polished there.
 #pragma unroll
     for (int r = 0; r < R; r++) {
         if (!active || r * G + s >= n) continue;
         cd zj = cmk(zre[r], zim[r]);
+        if (fabs(zj.im) <= 1e-12 * cabs_(zj)) zj.im = 0.0;
         polish_root(alpha, n, zj);
         zre[r] = zj.re; zim[r] = zj.im;
     }
@@ -327,12 +331,6 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
     for (int k = 0; k < 4; k++)
         z[k] = G == 1 ? cmk(zre[k / G], zim[k / G])
                       : cmk(__shfl_sync(full, zre[k / G], k % G, G), __shfl_sync(full, zim[k / G], k % G, G));
-}
-
-LCDM_HD void polish_real(const double* alpha, int n, double& x) {
-    cd r = cmk(x, 0.0);
-    polish_root(alpha, n, r);
-    x = r.re;
 }
 
 // Record of one cosmology from its parameter row p[ncol] = (H0, Om, OL, Or[, Ok]);
@@ -383,9 +381,8 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
         int nreal = 0, ir[4], ic[4], ncx = 0;
         #pragma unroll 1
         for (int i = 0; i < n; i++) {
-            if (triple0 || fabs(z[i].im) <= 1e-12 * cabs_(z[i])) {
+            if (triple0 || fabs(z[i].im) <= 1e-12 * cabs_(z[i])) {   // (polished on the axis already)
                 z[i].im = 0;
-                if (!triple0) polish_real(alpha, n, z[i].re);
                 ir[nreal++] = i;
             }
             else ic[ncx++] = i;
