@@ -345,20 +345,29 @@ __device__ __forceinline__ double acc_to_double(double v) { return v; }
 __device__ __forceinline__ double acc_to_double(df64 v) { return (double)v.hi + (double)v.lo; }
 
 // Warp sum of the per-lane accumulators of one row, added to the row's FP64 sums.
+// acc[i * ACC_STRIDE]: the lane's accumulators in shared memory.
+enum { ACC_STRIDE = 256 };
 template <int NV, int K, class AccT>
 __device__ __forceinline__ void flush_row(const AccT* acc, int64_t row, const PairArgs& a, int lane, int64_t warp,
                                           int64_t wf, int64_t wl) {
     double v[NV];
 #pragma unroll
     for (int i = 0; i < NV; i++) {
-        v[i] = acc_to_double(acc[i]);
+        v[i] = acc_to_double(acc[i * ACC_STRIDE]);
         for (int off = 16; off > 0; off >>= 1) v[i] += __shfl_down_sync(0xffffffffu, v[i], off);
     }
     if (lane == 0) add_row(a, row, v, K + 1, warp, wf, wl);
 }
 
+// Register budget: the FP32 kernels are bound by how many warps hide the
+// latency of their dependent chains, so the three-tangent kernel is held to
+// 128 registers (two full blocks per SM, a few spills) and the value kernel
+// to 85 (three), which measured faster than the unconstrained allocation.
+template <int PREC, int K>
+struct MinBlocks { enum { value = PREC == 1 ? (K == 3 ? 2 : (K == 0 ? 3 : 1)) : 1 }; };
+
 template <int PREC, int K, bool WT, bool WX>
-__global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
+__global__ void __launch_bounds__(256, MinBlocks<PREC, K>::value) pairs_kernel(PairArgs a) {
     typedef typename std::conditional<PREC == 0, double, float>::type TO;
     constexpr int NV = K + 2;   // H0, K Omega directions, loglike value
     const int lane = threadIdx.x & 31;
@@ -372,10 +381,14 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
     const TO Mobs = (TO)a.M;
     typedef typename std::conditional<PREC == 0, double, df64>::type AccT;
     int64_t row = -1;
-    AccT acc[NV];
+    // The per-lane accumulators live in shared memory (lane-private slots):
+    // they would otherwise stay in registers through the whole pair
+    // evaluation, where registers bound the number of resident warps.
+    __shared__ AccT acc_s[NV * ACC_STRIDE];
+    AccT* acc = acc_s + threadIdx.x;
     int64_t acc_row = -1;
 #pragma unroll
-    for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
+    for (int i = 0; i < NV; i++) acc[i * ACC_STRIDE] = cst<AccT>(0.0);
     // deterministic reduction: the warp's first and last rows, its slots zeroed
     int64_t wf = -1, wl = -1;
     if (a.part && reduce && warp < a.det_cap) {
@@ -476,13 +489,13 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
         const bool uniform = __all_sync(0xffffffffu, row == r0);
         if (uniform && r0 == acc_row) {
 #pragma unroll
-            for (int i = 0; i < NV; i++) acc[i] = acc[i] + c[i];
+            for (int i = 0; i < NV; i++) acc[i * ACC_STRIDE] = acc[i * ACC_STRIDE] + c[i];
             continue;
         }
         if (acc_row >= 0) flush_row<NV, K>(acc, acc_row, a, lane, warp, wf, wl);
         if (uniform) {
 #pragma unroll
-            for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0) + c[i];
+            for (int i = 0; i < NV; i++) acc[i * ACC_STRIDE] = cst<AccT>(0.0) + c[i];
             acc_row = r0;
         } else {
             double cd_[NV];
@@ -490,7 +503,7 @@ __global__ void __launch_bounds__(256) pairs_kernel(PairArgs a) {
             for (int i = 0; i < NV; i++) cd_[i] = (double)c[i];
             if (seg_reduce<NV>(cd_, row) && active) add_row(a, row, cd_, K + 1, warp, wf, wl);
 #pragma unroll
-            for (int i = 0; i < NV; i++) acc[i] = cst<AccT>(0.0);
+            for (int i = 0; i < NV; i++) acc[i * ACC_STRIDE] = cst<AccT>(0.0);
             acc_row = -1;
         }
     }

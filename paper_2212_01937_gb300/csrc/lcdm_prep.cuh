@@ -437,27 +437,47 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
             //   d rho_j / d theta_k = -(dE^2/dtheta_k)(rho_j) / (alpha_n prod_{m != j} (rho_j - rho_m)),
             // with dE^2/dOm = x^3, dE^2/dOL = 1, dE^2/dOr = x^4, dE^2/dOk = dE^2/dOs = x^2,
             // dE^2/dOx = x, and -x^2 added to the first three under the closure.
+            // With G lanes per cosmology, lane j of the group takes root j and
+            // the group exchanges the results (the G lanes of a group take the
+            // same branches: one cosmology).
             cd dr[4][RF_KT];
+            const int sg = G > 1 ? (int)(threadIdx.x & (G - 1)) : 0;
+            int degen = 0;
             #pragma unroll 1
             for (int j = 0; j < nr; j++) {
-                const cd x = rho[j], x2 = cmul(x, x), x3 = cmul(x2, x), x4 = cmul(x3, x);
+                if (G > 1 && j != sg) continue;
+                const cd x = rho[j], x2 = cmul(x, x);
                 cd e2p = cmk(an, 0);
                 #pragma unroll 1
                 for (int m2 = 0; m2 < nr; m2++)
                     if (m2 != j) e2p = cmul(e2p, csub(x, rho[m2]));
                 const bool degenerate = e2p.re == 0 && e2p.im == 0;
-                if (degenerate && !triple0) st = (st == ST_OK) ? ST_DEGENERATE : st;
+                if (degenerate) degen = 1;
                 const cd inv = degenerate ? cmk(nan(""), nan("")) : crcp(e2p);
-                const double cl = ncol == 4 ? 1.0 : 0.0;
-                const cd g[RF_KT] = {csub(x3, cmul(cmk(cl, 0), x2)), csub(cmk(1, 0), cmul(cmk(cl, 0), x2)),
-                                     csub(x4, cmul(cmk(cl, 0), x2)), x2, x2, x};
+                const cd x3 = cmul(x2, x);
+                const cd cx2 = ncol == 4 ? x2 : cmk(0, 0);
                 #pragma unroll 1
                 for (int k = 0; k < K; k++) {
-                    cd d = cmul(g[k], inv);
+                    const cd g = k == 0 ? csub(x3, cx2) : k == 1 ? csub(cmk(1, 0), cx2)
+                               : k == 2 ? csub(cmul(x3, x), cx2) : k == 5 ? x : x2;
+                    cd d = cmul(g, inv);
                     dr[j][k] = cmk(-d.re, -d.im);
                     if (n == 3 && k == 2) dr[j][k] = cmk(nan(""), nan(""));  // no Or direction in a cubic
                 }
             }
+            if (G > 1) {
+                const unsigned gmask = ((1u << G) - 1) << ((threadIdx.x & 31) & ~(G - 1));
+                #pragma unroll
+                for (int o = 1; o < G; o <<= 1) degen |= __shfl_xor_sync(gmask, degen, o, G);
+                #pragma unroll 1
+                for (int j = 0; j < nr; j++)
+                    #pragma unroll 1
+                    for (int k = 0; k < K; k++) {
+                        dr[j][k].re = __shfl_sync(gmask, dr[j][k].re, j, G);
+                        dr[j][k].im = __shfl_sync(gmask, dr[j][k].im, j, G);
+                    }
+            }
+            if (degen && !triple0) st = (st == ST_OK) ? ST_DEGENERATE : st;
             // big-root quantities of the quartic, scaled by lam = Or (see quartic_integrals)
             if (n == 4) {
                 double rA = A.re;                  // rho_A
@@ -503,12 +523,13 @@ template <int G> __device__ int prep_one(const double* p, int ncol, double* rec,
                 }
                 const int jq = n == 4 ? 2 : 1;
                 if (cpair) {
-                    cd r = cmk(P1.re - 1.0, P1.im), r2 = cmul(r, r);
+                    cd r = cmk(P1.re - 1.0, P1.im);
                     cd q = cdiv(cmk(-1.0, 0.0), r);
                     rec[RF_QPRE] = q.re;
                     rec[RF_QPIM] = q.im;
+                    const cd q2 = cmul(q, q);   // dq = dr / r^2 = q^2 dr
                     for (int k = 0; k < K; k++) {
-                        cd dq = cdiv(dr[jq][k], r2);
+                        cd dq = cmul(dr[jq][k], q2);
                         rec[RF_DQPRE + k] = dq.re;
                         rec[RF_DQPIM + k] = dq.im;
                     }
