@@ -146,7 +146,7 @@ template <class S> LCDM_HD S phi_rc(const S& w, int* fail) {
 //   eq. (3.9):  X H0/c = z [ T0 + (2 rho_B^2 - |P-B|^2) R_F + rho_A G ]
 // with u~ = sqrt(lam) u and the terms defined in the code.
 template <class S, class PS, bool WT, bool WX>
-LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
+LCDM_HD void quartic_integrals(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
                                const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, const S& qA,
                                const S& qB, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX, int* fail) {
     typedef typename Base<S>::type T;
@@ -236,7 +236,7 @@ LCDM_NI void quartic_integrals(typename Base<S>::type z, const S& lam, const S& 
 }
 
 template <class S, class PS, bool WT, bool WX>
-LCDM_NI void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, const S& YA, const PS& YP,
+LCDM_HD void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, const S& YA, const PS& YP,
                              const S& amh, const S& qA, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX,
                              int* fail) {
     typedef typename Base<S>::type T;

@@ -24,7 +24,11 @@
 #ifndef LCDM_HD
 #define LCDM_HD __device__ __forceinline__
 #endif
-// heavy routines are real calls: each instantiation is optimised once
+// Routines off the main path (R_C by duplication and its fallbacks) are real
+// calls, compiled once per instantiation.  The main path (the integrals and
+// the shared duplication sequence) is inlined into the kernels: with the
+// kernels' register caps the allocator then sees the whole pair at once,
+// with no argument passing through local memory (measured faster).
 #ifndef LCDM_NI
 #define LCDM_NI __device__ __noinline__
 #endif
@@ -639,7 +643,7 @@ struct SymResult {
 };
 
 template <class T, int NJ, bool WANT_D, bool DDL = false>
-LCDM_NI SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, const T* dj, int* fail, T hl = T(),
+LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, const T* dj, int* fail, T hl = T(),
                                      T PiL = T()) {
     static_assert(!DDL || (WANT_D && NJ > 0), "the divided-difference track needs R_D and an R_J track");
     SymResult<T, NJ> R;

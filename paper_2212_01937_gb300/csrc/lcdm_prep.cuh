@@ -314,18 +314,37 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
             if (__all_sync(full, done)) break;
         }
     }
-    // Newton polishing on the original coefficients (the monic ones carry the
-    // rounding of the division by alpha_n), evaluated by the compensated
-    // scheme, each root by the lane that owns it.  A root whose imaginary part
-    // is negligible (|Im| <= 1e-12 |z|: the classification's test) is put on
-    // the real axis first and polished there.
+    // A root whose imaginary part is negligible (|Im| <= 1e-12 |z|: the
+    // classification's test) is put on the real axis.  Roots closer than a
+    // tenth of their modulus to another root (near-multiple roots, as near
+    // the no-Big-Bang boundary) are then polished by Newton steps on the
+    // original coefficients (the monic ones carry the rounding of the
+    // division by alpha_n), evaluated by the compensated scheme, each by the
+    // lane that owns it; an isolated root is already within an ulp or two
+    // after the sweeps (the rounding of the monic coefficients moves it by
+    // its condition number, small when it is isolated), so it skips the
+    // polish and its FP64 work.
+    {
+        double cr[4], ci[4];
 #pragma unroll
-    for (int r = 0; r < R; r++) {
-        if (!active || r * G + s >= n) continue;
-        cd zj = cmk(zre[r], zim[r]);
-        if (fabs(zj.im) <= 1e-12 * cabs_(zj)) zj.im = 0.0;
-        polish_root(alpha, n, zj);
-        zre[r] = zj.re; zim[r] = zj.im;
+        for (int k = 0; k < 4; k++) {
+            cr[k] = G == 1 ? zre[k / G] : __shfl_sync(full, zre[k / G], k % G, G);
+            ci[k] = G == 1 ? zim[k / G] : __shfl_sync(full, zim[k / G], k % G, G);
+        }
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int j = r * G + s;
+            if (!active || j >= n) continue;
+            cd zj = cmk(zre[r], zim[r]);
+            const double mz = cabs_(zj);
+            if (fabs(zj.im) <= 1e-12 * mz) zj.im = 0.0;
+            bool isolated = true;
+#pragma unroll 1
+            for (int k = 0; k < n; k++)
+                if (k != j && !(cabs_(csub(cmk(cr[k], ci[k]), cmk(cr[j], ci[j]))) > 0.1 * mz)) isolated = false;
+            if (!isolated) polish_root(alpha, n, zj);
+            zre[r] = zj.re; zim[r] = zj.im;
+        }
     }
 #pragma unroll
     for (int k = 0; k < 4; k++)
