@@ -279,6 +279,39 @@ LCDM_HD void cubic_integrals(typename Base<S>::type z, const S& A, const PS& P, 
     }
 }
 
+// The same integrals as one real call, for the kernels whose tangents or
+// outputs need more registers than the inlined path can hold (seven-column
+// tangents, X's tangents): there the allocator handles the pair in two parts.
+template <class S, class PS, bool WT, bool WX>
+LCDM_NI void quartic_integrals_call(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
+                                    const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, const S& qA,
+                                    const S& qB, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX, int* fail) {
+    quartic_integrals<S, PS, WT, WX>(z, lam, aA, mA, epsA, rhoA, B, P, YB, YP, qA, qB, wP, nrm, Ichi, It, IX, fail);
+}
+template <class S, class PS, bool WT, bool WX>
+LCDM_NI void cubic_integrals_call(typename Base<S>::type z, const S& A, const PS& P, const S& YA, const PS& YP,
+                                  const S& amh, const S& qA, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX,
+                                  int* fail) {
+    cubic_integrals<S, PS, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
+}
+
+template <bool CALL, class S, class PS, bool WT, bool WX>
+LCDM_HD void quartic_integrals_any(typename Base<S>::type z, const S& lam, const S& aA, const S& mA, const S& epsA,
+                                   const S& rhoA, const S& B, const PS& P, const S& YB, const PS& YP, const S& qA,
+                                   const S& qB, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX, int* fail) {
+    if constexpr (CALL)
+        quartic_integrals_call<S, PS, WT, WX>(z, lam, aA, mA, epsA, rhoA, B, P, YB, YP, qA, qB, wP, nrm, Ichi, It, IX, fail);
+    else
+        quartic_integrals<S, PS, WT, WX>(z, lam, aA, mA, epsA, rhoA, B, P, YB, YP, qA, qB, wP, nrm, Ichi, It, IX, fail);
+}
+template <bool CALL, class S, class PS, bool WT, bool WX>
+LCDM_HD void cubic_integrals_any(typename Base<S>::type z, const S& A, const PS& P, const S& YA, const PS& YP,
+                                 const S& amh, const S& qA, const PS& wP, const S& nrm, S& Ichi, S& It, S& IX,
+                                 int* fail) {
+    if constexpr (CALL) cubic_integrals_call<S, PS, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
+    else cubic_integrals<S, PS, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
+}
+
 // ------------------------------------------------------ z -> infinity ------
 // The upper limit at infinity (Sec. 2.1.1: the age t(0, inf); the comoving
 // distance to the particle horizon chi(0, inf)) of the quantities above, with

@@ -140,6 +140,8 @@ template <> LCDM_HD float one_plus_qz<float>(const double*, const float2* rf, in
 // Build the root quantities in scalar S and evaluate the integrals.
 template <class T, int K, bool WT, bool WX> struct PairEval {
     typedef typename std::conditional<(K > 0), Dual<T, K>, T>::type S;
+    // the integrals inline, or as one call (see quartic_integrals_call)
+    static constexpr bool SPLIT = K > 3 || (K > 0 && WX);
 
     static LCDM_HD S val(const double* rd, const float2* rf, int i, int di) {
         S s;
@@ -200,12 +202,12 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
             if (kind == 0) {
                 S B = val(rd, rf, RF_B, RF_DB);
                 S YB = yval(rd, rf, RF_YB, B);
-                quartic_integrals<S, CPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
+                quartic_integrals_any<SPLIT, S, CPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
                                                        val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
                                                        val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, qA,
                                                        val(rd, rf, RF_QB, RF_DQB), wP, nrm, Ichi, It, IX, fail);
             } else {
-                cubic_integrals<S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
+                cubic_integrals_any<SPLIT, S, CPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
             }
         } else {
             wim = wim + cst<T>(1.0);
@@ -216,12 +218,12 @@ template <class T, int K, bool WT, bool WX> struct PairEval {
             if (kind == 1) {
                 S B = val(rd, rf, RF_B, RF_DB);
                 S YB = yval(rd, rf, RF_YB, B);
-                quartic_integrals<S, RPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
+                quartic_integrals_any<SPLIT, S, RPair<S>, WT, WX>(z, val(rd, rf, RF_LAM, RF_DLAM), val(rd, rf, RF_AA, RF_DAA),
                                                        val(rd, rf, RF_MA, RF_DMA), val(rd, rf, RF_EPSA, RF_DEPSA),
                                                        val(rd, rf, RF_RHOA, RF_DRHOA), B, P, YB, YP, qA,
                                                        val(rd, rf, RF_QB, RF_DQB), wP, nrm, Ichi, It, IX, fail);
             } else {
-                cubic_integrals<S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
+                cubic_integrals_any<SPLIT, S, RPair<S>, WT, WX>(z, A, P, YA, YP, amh, qA, wP, nrm, Ichi, It, IX, fail);
             }
         }
     }
@@ -365,11 +367,12 @@ __device__ __forceinline__ void flush_row(const AccT* acc, int64_t row, const Pa
 // which measured faster than the unconstrained allocation (the tangent
 // kernel of the benchmark step: 0.51 ms against 0.62 ms, with the pair's
 // integrals inlined).
-template <int PREC, int K>
-struct MinBlocks { enum { value = PREC == 1 ? (K == 3 ? 2 : (K == 0 ? 3 : 1)) : 1 }; };
+// (The kernels with X's tangents need more: they are left unconstrained.)
+template <int PREC, int K, bool WX>
+struct MinBlocks { enum { value = PREC == 1 ? ((K == 3 && !WX) ? 2 : (K == 0 ? 3 : 1)) : 1 }; };
 
 template <int PREC, int K, bool WT, bool WX>
-__global__ void __launch_bounds__(256, MinBlocks<PREC, K>::value) pairs_kernel(PairArgs a) {
+__global__ void __launch_bounds__(256, MinBlocks<PREC, K, WX>::value) pairs_kernel(PairArgs a) {
     typedef typename std::conditional<PREC == 0, double, float>::type TO;
     constexpr int NV = K + 2;   // H0, K Omega directions, loglike value
     const int lane = threadIdx.x & 31;
