@@ -39,12 +39,13 @@ COT_OUTPUTS = ("d_C", "t", "mu")
 # add/sub + mul, and div + sqrt + transcendental (the special-function unit).
 ALG_FLOP_PER_PAIR = 7033.1
 ALG_MUFU_PER_PAIR = 390.3
-# FP32 floating-point operations the kernel executes per pair (FFMA counted as
-# 2, FADD and FMUL as 1) and DRAM bytes (read + write) per launch, from an ncu
-# capture of this kernel on this workload (None until re-taken after a change
-# of the kernel).
-EXEC_FLOP_PER_PAIR = None
-TRAFFIC_BYTES = None
+# FP32 floating-point operations the step's two pair launches execute per pair
+# (FFMA counted as 2, FADD and FMUL as 1: 685 in the value launch + 2342 in the
+# tangent launch) and their DRAM bytes (read + write) per step, from one ncu
+# capture of both launches on this workload (profiles/pairs_kernel_fp32_vjp_
+# 4096x1024.md; to be set to None whenever the kernels change until re-taken).
+EXEC_FLOP_PER_PAIR = 3026.7
+TRAFFIC_BYTES = 110.7e6
 # Derived peaks (unit counts x maximum SM clock): FP32 FMA, 152 SMs x 128 lanes
 # x 2 flops; special-function unit, 152 SMs x 16 per clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -404,7 +405,8 @@ def main():
                 "mufu": {"achieved_gops": mufu, "peak_gops": MUFU_PEAK_GOPS, "frac": mufu / MUFU_PEAK_GOPS,
                          "frac_of_measured": mufu / meas["mufu_gops"]},
                 "measured_peaks": meas,
-                "kernel": "pairs_kernel<FP32,K=3,t,X>", "kernel_ms": pair_ms, "prep_ms": prep_ms,
+                "kernel": "pairs_kernel<FP32,K=0,X> + pairs_kernel<FP32,K=3,t> (the step's two pair launches)",
+                "kernel_ms": pair_ms, "prep_ms": prep_ms,
                 "peak_note": "FP32 FMA issue: 152 SMs x 128 lanes x 2 x 2.07 GHz (derived from unit counts and "
                              "the maximum clock; MEASURED_PEAKS has HBM and bf16 only)"}
         extra = {}
