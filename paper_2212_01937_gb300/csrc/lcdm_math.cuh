@@ -18,6 +18,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 // Function qualifiers (overridable: the arithmetic is plain C++ and also
 // compiles for the host).
@@ -463,6 +464,22 @@ LCDM_HD int even_exponent(float mag) {
     return e & ~1;
 }
 
+// 2^k exactly, from its bit pattern (|k| <= 126: a normal number in either
+// precision).  Multiplying by it is exact and, unlike ldexp, one instruction.
+template <class B> LCDM_HD B pow2i(int k);
+template <> LCDM_HD float pow2i<float>(int k) {
+    const uint32_t b = (uint32_t)(k + 127) << 23;
+    float f;
+    memcpy(&f, &b, sizeof f);
+    return f;
+}
+template <> LCDM_HD double pow2i<double>(int k) {
+    const uint64_t b = (uint64_t)(k + 1023) << 52;
+    double f;
+    memcpy(&f, &b, sizeof f);
+    return f;
+}
+
 // One duplication sequence for R_F, R_D (x1 special when WANT_D; the pair
 // members special as well when WANT_DP) and NJ R_J tracks with p_j > 0.  The
 // triple is (x1, pair).  Arguments are first scaled by an even power of two
@@ -661,26 +678,31 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
         const float a = fabsf((float)sval(p[j]));
         if (a > mag) mag = a;
     }
-    // scale by 2^-e, e even: x, y, p by 2^-e, square roots by 2^-e/2
-    const int e = even_exponent(mag);
-    s1 = sldexp(s1, -e / 2);
-    S = sldexp(S, -e / 2);
-    P = sldexp(P, -e);
+    // scale by 2^-e, e even: x, y, p by g = 2^-e, square roots by h = 2^-e/2;
+    // the results scale back by h (R_F) and h g (R_D, R_J), h g g (DJ), one
+    // factor at a time so that every factor is a normal number
+    typedef typename Base<T>::type BT;
+    int e = even_exponent(mag);
+    e = e > 124 ? 124 : (e < -124 ? -124 : e);
+    const BT h = pow2i<BT>(-e / 2), g = pow2i<BT>(-e);
+    s1 = s1 * h;
+    S = S * h;
+    P = P * g;
     T x1 = s1 * s1;
     T sig = S * S - cst<T>(2.0) * P;   // exact enough for the first stopping test (see above)
     T pi = P * P;
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        p[j] = sldexp(p[j], -e);
-        delta[j] = sldexp(dj[j], -3 * e);
+        p[j] = p[j] * g;
+        delta[j] = dj[j] * g * g * g;
         sJ[j] = cst<T>(0.0);
     }
     T sD1 = cst<T>(0.0);
     T f = cst<T>(1.0);
     T hs = cst<T>(0.0), sDD = cst<T>(0.0);
     if (DDL) {
-        hs = sldexp(hl, -e);
-        PiL = sldexp(PiL, -2 * e);
+        hs = hl * g;
+        PiL = PiL * g * g;
     }
     const T tol = Prec<T>::tol();
     int m = 0;
@@ -744,14 +766,14 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
         T e2 = X * sY + pY, e3 = X * pY;
         T ser = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
                 - e2 * e3 * cst<T>(3.0 / 44.0);
-        R.RF = sldexp(ser / ssqrt(A), -e / 2);
+        R.RF = ser / ssqrt(A) * h;
     }
     if (WANT_D) {
         T A = (sig + cst<T>(3.0) * x1) * cst<T>(0.2), iA = cst<T>(1.0) / A;
         T X = (A - x1) * iA;
         T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
         T ser = rj_series<T, T>(X, sY, pY, X);
-        R.RD1 = sldexp(f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1, -3 * e / 2);
+        R.RD1 = (f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1) * g * h;
     } else {
         R.RD1 = R.RF;
     }
@@ -761,7 +783,7 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
         T X = (A - x1) * iA, Pp = (A - p[j]) * iA;
         T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
         T ser = rj_series<T, T>(X, sY, pY, Pp);
-        R.RJ[j] = sldexp(f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j], -3 * e / 2);
+        R.RJ[j] = (f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j]) * g * h;
     }
     R.DJ = R.RD1;
     if (DDL) {
@@ -782,7 +804,7 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
         T a32_1 = iA1 / r1, a32_2 = iA2 / r2;
         T dA32 = cst<T>(-0.4) * (A1 + r1 * r2 + A2) / (r1 + r2) * a32_1 * a32_2;
         T dser = dA32 * ser.v1 + a32_2 * ser.d;
-        R.DJ = sldexp(f * f * dser + cst<T>(6.0) * sDD, -5 * e / 2);
+        R.DJ = (f * f * dser + cst<T>(6.0) * sDD) * g * g * h;
         R.RJ[NJ - 1] = R.RD1 + hl * R.DJ;
     }
     return R;
