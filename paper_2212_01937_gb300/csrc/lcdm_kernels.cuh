@@ -47,6 +47,11 @@ enum CosmoStatus {
 };
 
 // ------------------------------------------------------------ observables ---
+LCDM_HD float expm1_(float x) { return expm1f(x); }
+LCDM_HD double expm1_(double x) { return expm1(x); }
+LCDM_HD void sincos_(float x, float* s, float* c) { sincosf(x, s, c); }
+LCDM_HD void sincos_(double x, double* s, double* c) { sincos(x, s, c); }
+
 // S_k(D): sinh / sin form, or its Taylor series in u = Ok D^2 near flatness,
 // with dS/dD and dS/dOk ([59] eqs. 13.47, 13.57 as cited in Sec. 2.1.1).
 template <class T> LCDM_HD void curv_map(T D, T Ok, T& S, T& SD, T& Sk) {
@@ -68,11 +73,16 @@ template <class T> LCDM_HD void curv_map(T D, T Ok, T& S, T& SD, T& Sk) {
         return;
     }
     if (Ok > 0) {
+        // sinh and cosh from one exponential: e^x - 1 = m, sinh x = (m + m / (1 + m)) / 2
+        // (both terms positive for x = sqrt(Ok) D >= 0), cosh x = ((1 + m) + 1 / (1 + m)) / 2
         T r = sqrt(Ok);
-        S = sinh(r * D) / r; SD = cosh(r * D);
+        const T m = expm1_(r * D), ex = m + (T)1;
+        S = (m + m / ex) * (T)0.5 / r; SD = (ex + (T)1 / ex) * (T)0.5;
     } else {
         T r = sqrt(-Ok);
-        S = sin(r * D) / r; SD = cos(r * D);
+        T sn, cs;
+        sincos_(r * D, &sn, &cs);
+        S = sn / r; SD = cs;
     }
     Sk = (D * SD - S) / (2 * Ok);
 }

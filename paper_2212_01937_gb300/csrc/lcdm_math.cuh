@@ -87,8 +87,6 @@ template <> struct CstImpl<double> { static LCDM_HD double make(double v) { retu
 template <> struct CstImpl<df64> { static LCDM_HD df64 make(double v) { return df_from_double(v); } };
 template <class T> LCDM_HD T cst(double v) { return CstImpl<T>::make(v); }
 // exact multiplication by 2^e
-LCDM_HD float sldexp(float a, int e) { return ldexpf(a, e); }
-LCDM_HD double sldexp(double a, int e) { return ldexp(a, e); }
 
 // ---------------------------------------------------------------------------
 // Dual numbers (forward-mode tangents over K parameters)
@@ -170,12 +168,6 @@ template <class T, int K> LCDM_HD void dacc(Dual<T, K>& r, T g, const Dual<T, K>
 template <class T, int K> struct CstImpl<Dual<T, K> > {
     static LCDM_HD Dual<T, K> make(double v) { return dconst<T, K>(CstImpl<T>::make(v)); }
 };
-template <class T, int K> LCDM_HD Dual<T, K> sldexp(const Dual<T, K>& a, int e) {
-    Dual<T, K> r; r.v = sldexp(a.v, e);
-#pragma unroll
-    for (int k = 0; k < K; k++) r.d[k] = sldexp(a.d[k], e);
-    return r;
-}
 // base scalar of a (possibly dual) scalar, and constants of that base type
 template <class S> struct Base { typedef S type; };
 template <class T, int K> struct Base<Dual<T, K> > { typedef T type; };
@@ -295,10 +287,6 @@ template <class T> LCDM_HD float pmag(const RPair<T>& p) {
     float a = fabsf((float)sval(p.a)), b = fabsf((float)sval(p.b));
     return a > b ? a : b;
 }
-template <class T> LCDM_HD CPair<T> pldexp(const CPair<T>& p, int e) {
-    return mkcp(mkcx<T>(sldexp(p.c.re, e), sldexp(p.c.im, e)));
-}
-template <class T> LCDM_HD RPair<T> pldexp(const RPair<T>& p, int e) { return mkrp<T>(sldexp(p.a, e), sldexp(p.b, e)); }
 
 // ---------------------------------------------------------------------------
 // Carlson's duplication algorithm (ref. [10]).
@@ -459,8 +447,13 @@ LCDM_HD bool group_any(bool p) {
 #endif
 }
 
+// Even exponent of the largest argument (0 for zero, subnormal or non-finite
+// magnitudes), read from the float's exponent bits.
 LCDM_HD int even_exponent(float mag) {
-    int e = (mag > 0.f && mag < 3.0e38f) ? ilogbf(mag) : 0;
+    uint32_t b;
+    memcpy(&b, &mag, sizeof b);
+    const int be = (int)((b >> 23) & 0xffu);
+    const int e = (be == 0 || be == 0xff) ? 0 : be - 127;
     return e & ~1;
 }
 
@@ -501,13 +494,16 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         float a = fabsf((float)sval(p[j]));
         if (a > mag) mag = a;
     }
-    const int e = even_exponent(mag);
-    x1 = sldexp(x1, -e);
-    pr = pldexp(pr, -e);
+    typedef typename Base<T>::type BT;
+    int e = even_exponent(mag);
+    e = e > 124 ? 124 : (e < -124 ? -124 : e);
+    const BT h = pow2i<BT>(-e / 2), g = pow2i<BT>(-e);   // exact scale factors (see carlson_sym)
+    x1 = x1 * g;
+    pr = pscale(pr, g);
     T delta[NJ > 0 ? NJ : 1], sJ[NJ > 0 ? NJ : 1];
 #pragma unroll
     for (int j = 0; j < NJ; j++) {
-        p[j] = sldexp(p[j], -e);
+        p[j] = p[j] * g;
         delta[j] = (p[j] - x1) * pprod(prsub(p[j], pr));
         sJ[j] = cst<T>(0.0);
     }
@@ -517,7 +513,7 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
     // divided-difference track: h = p_last - x1 (scaled), Pi = prod(p_last - pair)
     T hs = cst<T>(0.0), sDD = cst<T>(0.0), PiL = cst<T>(0.0);
     if (DDL) {
-        hs = sldexp(hl, -e);
+        hs = hl * g;
         PiL = pprod(prsub(p[NJ - 1], pr));
     }
     const T tol = Prec<T>::tol();
@@ -581,16 +577,16 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         T e2 = X * psum(Y) + pprod(Y), e3 = X * pprod(Y);
         T ser = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
                 - e2 * e3 * cst<T>(3.0 / 44.0);
-        R.RF = sldexp(ser / ssqrt(A), -e / 2);
+        R.RF = ser / ssqrt(A) * h;
     }
     if (WANT_D) {
         T A = (psum(pr) + cst<T>(3.0) * x1) * cst<T>(0.2), iA = cst<T>(1.0) / A;
         T X = (A - x1) * iA;
         PT Y = pscale(prsub(A, pr), iA);
         T ser = rj_series<T, T>(X, psum(Y), pprod(Y), X);
-        R.RD1 = sldexp(f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1, -3 * e / 2);
+        R.RD1 = (f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1) * g * h;
     }
-    if (WANT_DP) R.RDp = pldexp(rd_pair_series(x1, pr, f, sDp), -3 * e / 2);
+    if (WANT_DP) R.RDp = pscale(pscale(rd_pair_series(x1, pr, f, sDp), g), h);
     else R.RDp = pzero(pr);
 #pragma unroll
     for (int j = 0; j < (DDL ? NJ - 1 : NJ); j++) {
@@ -598,7 +594,7 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         T X = (A - x1) * iA, P = (A - p[j]) * iA;
         PT Y = pscale(prsub(A, pr), iA);
         T ser = rj_series<T, T>(X, psum(Y), pprod(Y), P);
-        R.RJ[j] = sldexp(f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j], -3 * e / 2);
+        R.RJ[j] = (f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j]) * g * h;
     }
     if (DDL) {
         // final series: A(u) = (sig + 2u)/5 at u1 = p, u2 = x1; X = 1 - x1/A,
@@ -622,7 +618,7 @@ LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T 
         T dser = dA32 * ser.v1 + a32_2 * ser.d;          // [A^-3/2 S]
         // R_J(p) - R_D = f (T(u1) - T(u2)) + 6 (sum_p - sum_x1), T = A^-3/2 S,
         // with u1 - u2 = f hs and the sums' difference = hs sDD
-        R.DJ = sldexp(f * f * dser + cst<T>(6.0) * sDD, -5 * e / 2);
+        R.DJ = (f * f * dser + cst<T>(6.0) * sDD) * g * g * h;
         // R_J(x1 + hl) = R_D(x2, x3, x1) + hl DJ: a sum, no cancellation
         R.RJ[NJ - 1] = R.RD1 + hl * R.DJ;
     }
