@@ -9,12 +9,12 @@
 //  * CPair/RPair the two roots (or integral arguments) that are either a complex
 //                conjugate pair or two reals, with the operations the formulas
 //                need (sum and product of the members are real in both cases).
-//  * carlson_dup one duplication sequence on (x1, x2, x3) shared by R_F, the
-//                three R_D with each argument in turn as the special one, up to
-//                two R_J tracks (eqs. 2.6-2.9), after Carlson's duplication
-//                algorithm (the paper's ref. [10]), and optionally the divided
-//                difference of the last R_J track against R_D; generic over
-//                plain and dual numbers.
+//  * carlson_sym one duplication sequence on (x1, y_a, y_b) shared by R_F,
+//                R_D (x1 special) and up to two R_J tracks (eqs. 2.6-2.9),
+//                after Carlson's duplication algorithm (the paper's ref. [10]),
+//                carried on the pair's symmetric functions, and optionally the
+//                divided difference of the last R_J track against R_D; generic
+//                over plain and dual numbers.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -269,25 +269,6 @@ template <class T, int K> LCDM_HD CPair<T> pval(const CPair<Dual<T, K> >& p) { r
 template <class T, int K> LCDM_HD RPair<T> pval(const RPair<Dual<T, K> >& p) { return mkrp<T>(p.a.v, p.b.v); }
 template <class T> LCDM_HD CPair<T> pval(const CPair<T>& p) { return p; }
 template <class T> LCDM_HD RPair<T> pval(const RPair<T>& p) { return p; }
-// largest squared distance of a member from a real point
-template <class T> LCDM_HD T pdev2(const CPair<T>& p, T mu) {
-    T d = p.c.re - mu; return d * d + p.c.im * p.c.im;
-}
-template <class T> LCDM_HD T pdev2(const RPair<T>& p, T mu) {
-    T da = p.a - mu, db = p.b - mu;
-    T a2 = da * da, b2 = db * db;
-    return sval(a2) > sval(b2) ? a2 : b2;
-}
-// largest member modulus (for scaling)
-template <class T> LCDM_HD float pmag(const CPair<T>& p) {
-    float r = fabsf((float)sval(p.c.re)), i = fabsf((float)sval(p.c.im));
-    return r > i ? r : i;
-}
-template <class T> LCDM_HD float pmag(const RPair<T>& p) {
-    float a = fabsf((float)sval(p.a)), b = fabsf((float)sval(p.b));
-    return a > b ? a : b;
-}
-
 // ---------------------------------------------------------------------------
 // Carlson's duplication algorithm (ref. [10]).
 // Deviation tolerance: the iteration stops once every argument is within
@@ -377,11 +358,6 @@ template <class U, class T> LCDM_HD U rj_series(U X, U sumY, U prodY, U P) {
     return cst<T>(1.0) - E2 * cst<T>(3.0 / 14.0) + E3 * cst<T>(1.0 / 6.0) + E2 * E2 * cst<T>(9.0 / 88.0)
            - E4 * cst<T>(3.0 / 22.0) - E2 * E3 * cst<T>(9.0 / 52.0) + E5 * cst<T>(3.0 / 26.0);
 }
-// complex x real helpers for the pair-special R_D series
-template <class T> LCDM_HD Cx<T> operator*(const Cx<T>& a, const T& s) { return mkcx<T>(a.re * s, a.im * s); }
-template <class T> LCDM_HD Cx<T> operator+(const Cx<T>& a, const T& s) { return mkcx<T>(a.re + s, a.im); }
-template <class T> LCDM_HD Cx<T> operator-(const T& s, const Cx<T>& a) { return mkcx<T>(s - a.re, -a.im); }
-template <class T> LCDM_HD Cx<T> operator-(const Cx<T>& a, const T& s) { return mkcx<T>(a.re - s, a.im); }
 
 // Divided-difference numbers: the values of a quantity at two points u1, u2
 // and its divided difference (v1 - v2) / (u1 - u2), with the product rule
@@ -398,54 +374,6 @@ template <class T> LCDM_HD DD<T> operator*(const DD<T>& a, const T& c) { return 
 template <class T> LCDM_HD DD<T> operator+(const DD<T>& a, const T& c) { return mkdd<T>(a.v1 + c, a.v2 + c, a.d); }
 template <class T> LCDM_HD DD<T> operator-(const T& c, const DD<T>& a) { return mkdd<T>(c - a.v1, c - a.v2, -a.d); }
 template <class T> LCDM_HD DD<T> operator-(const DD<T>& a, const T& c) { return mkdd<T>(a.v1 - c, a.v2 - c, a.d); }
-
-template <class T, int NJ, class PT>
-struct DupResult {
-    T RF;      // R_F(x1, x2, x3)
-    T RD1;     // R_D(x2, x3, x1): x1 special
-    PT RDp;    // R_D(x1, x2, x3), R_D(x1, x2, x3): pair member special
-    T RJ[NJ];  // R_J(x1, x2, x3, p_j)
-    T DJ;      // (R_J(x1,x2,x3,p_last) - R_D(x2,x3,x1)) / (p_last - x1)  (when requested)
-};
-
-// R_D with a pair member special, from the final duplicated arguments.
-template <class T> LCDM_HD CPair<T> rd_pair_series(T x1, const CPair<T>& pr, T f, const CPair<T>& sDp) {
-    Cx<T> c = pr.c, cb = conj(pr.c);
-    Cx<T> A = mkcx<T>((x1 + c.re + c.re) * cst<T>(0.2), cst<T>(0.0)) + c * cst<T>(0.4);
-    Cx<T> iA = cxrcp(A);
-    Cx<T> X = (mkcx<T>(cst<T>(0.0), cst<T>(0.0)) + (A - x1)) * iA;
-    Cx<T> Ym = (A - c) * iA, Yo = (A - cb) * iA;
-    Cx<T> ser = rj_series<Cx<T>, T>(X, Ym + Yo, Ym * Yo, Ym);
-    Cx<T> sA = cxsqrt(A);
-    Cx<T> r = ser * f / (A * sA) + sDp.c * cst<T>(3.0);
-    return mkcp(r);
-}
-template <class T> LCDM_HD RPair<T> rd_pair_series(T x1, const RPair<T>& pr, T f, const RPair<T>& sDp) {
-    RPair<T> out;
-    {
-        T A = (x1 + pr.b + cst<T>(3.0) * pr.a) * cst<T>(0.2), iA = cst<T>(1.0) / A;
-        T X = (A - x1) * iA, Ym = (A - pr.a) * iA, Yo = (A - pr.b) * iA;
-        out.a = f * rj_series<T, T>(X, Ym + Yo, Ym * Yo, Ym) * iA / ssqrt(A) + cst<T>(3.0) * sDp.a;
-    }
-    {
-        T A = (x1 + pr.a + cst<T>(3.0) * pr.b) * cst<T>(0.2), iA = cst<T>(1.0) / A;
-        T X = (A - x1) * iA, Ym = (A - pr.b) * iA, Yo = (A - pr.a) * iA;
-        out.b = f * rj_series<T, T>(X, Ym + Yo, Ym * Yo, Ym) * iA / ssqrt(A) + cst<T>(3.0) * sDp.b;
-    }
-    return out;
-}
-template <class T> LCDM_HD CPair<T> pzero(const CPair<T>&) { return mkcp(mkcx<T>(cst<T>(0.0), cst<T>(0.0))); }
-template <class T> LCDM_HD RPair<T> pzero(const RPair<T>&) { return mkrp<T>(cst<T>(0.0), cst<T>(0.0)); }
-
-// Whether the predicate holds on any lane that runs this call together with
-// the calling lane (on the host: the caller's own predicate).
-LCDM_HD bool group_any(bool p) {
-#ifdef __CUDA_ARCH__
-    return __any_sync(__activemask(), p);
-#else
-    return p;
-#endif
-}
 
 // Even exponent of the largest argument (0 for zero, subnormal or non-finite
 // magnitudes), read from the float's exponent bits.
@@ -471,158 +399,6 @@ template <> LCDM_HD double pow2i<double>(int k) {
     double f;
     memcpy(&f, &b, sizeof f);
     return f;
-}
-
-// One duplication sequence for R_F, R_D (x1 special when WANT_D; the pair
-// members special as well when WANT_DP) and NJ R_J tracks with p_j > 0.  The
-// triple is (x1, pair).  Arguments are first scaled by an even power of two
-// (exact; R_F ~ s^-1/2, R_D and R_J ~ s^-3/2).
-// With DDL, the last track is p = x1 + hl (hl given separately, exactly) and
-// DJ = (R_J(p) - R_D(x2, x3, x1)) / hl is evaluated term by term (sum terms
-// and the final series) so that close p and x1 cause no cancellation.
-template <class T, int NJ, bool WANT_D, class PT, bool DDL = false, bool WANT_DP = WANT_D>
-LCDM_NI DupResult<T, NJ, PT> carlson_dup(T x1, PT pr, const T* pj, int* fail, T hl = T()) {
-    static_assert(!DDL || (WANT_D && NJ > 0), "the divided-difference track needs R_D and an R_J track");
-    DupResult<T, NJ, PT> R;
-    float mag = fabsf((float)sval(x1));
-    float pm = pmag(pr);
-    if (pm > mag) mag = pm;
-    T p[NJ > 0 ? NJ : 1];
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-        p[j] = pj[j];
-        float a = fabsf((float)sval(p[j]));
-        if (a > mag) mag = a;
-    }
-    typedef typename Base<T>::type BT;
-    int e = even_exponent(mag);
-    e = e > 124 ? 124 : (e < -124 ? -124 : e);
-    const BT h = pow2i<BT>(-e / 2), g = pow2i<BT>(-e);   // exact scale factors (see carlson_sym)
-    x1 = x1 * g;
-    pr = pscale(pr, g);
-    T delta[NJ > 0 ? NJ : 1], sJ[NJ > 0 ? NJ : 1];
-#pragma unroll
-    for (int j = 0; j < NJ; j++) {
-        p[j] = p[j] * g;
-        delta[j] = (p[j] - x1) * pprod(prsub(p[j], pr));
-        sJ[j] = cst<T>(0.0);
-    }
-    T sD1 = cst<T>(0.0);
-    PT sDp = pzero(pr);
-    T f = cst<T>(1.0);
-    // divided-difference track: h = p_last - x1 (scaled), Pi = prod(p_last - pair)
-    T hs = cst<T>(0.0), sDD = cst<T>(0.0), PiL = cst<T>(0.0);
-    if (DDL) {
-        hs = hl * g;
-        PiL = pprod(prsub(p[NJ - 1], pr));
-    }
-    const T tol = Prec<T>::tol();
-    int m = 0;
-#pragma unroll 1
-    for (; m < Prec<T>::maxit; m++) {
-        T mu = x1 + psum(pr);
-#pragma unroll
-        for (int j = 0; j < NJ; j++) mu = mu + p[j];
-        mu = mu * cst<T>(1.0 / (3 + NJ));
-        T lim = tol * mu;
-        T lim2 = lim * lim;
-        T dx = x1 - mu;
-        bool conv = sval(dx * dx) <= sval(lim2) && sval(pdev2(pr, mu)) <= sval(lim2);
-#pragma unroll
-        for (int j = 0; j < NJ; j++) {
-            T dp = p[j] - mu;
-            conv = conv && sval(dp * dp) <= sval(lim2);
-        }
-        if (conv) break;
-        T s1 = ssqrt(x1);
-        PT sp = psqrt(pr);
-        T lam = s1 * psum(sp) + pprod(sp);
-        if (WANT_D) sD1 = sD1 + f / (s1 * (x1 + lam));
-        if (WANT_DP) sDp = sDp + pscale(prcp(sp * padd(pr, lam)), f);
-#pragma unroll
-        for (int j = 0; j < NJ; j++) {
-            T sq = ssqrt(p[j]);
-            T d = (sq + s1) * pprod(padd(sp, sq));
-            T f3 = f * f * f;
-            T ee = f3 * delta[j] / (d * d);
-            // the divided-difference track's own R_J follows from R_D and DJ
-            if (!(DDL && j == NJ - 1)) sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
-            if (DDL && j == NJ - 1) {
-                // [R_C(1,1+e)/d_p - 1/d_x1] / h with e/h = f^3 Pi / d_p^2 and
-                // (d_p - d_x1)/h = f [g(a) + 2b (a + b + sum sqrt(pair))] / (a + b),
-                // a = sqrt(p), b = sqrt(x1), g(v) = prod(v + sqrt(pair)), d_x1 = 2 b g(b)
-                T eh = f3 * PiL / (d * d);
-                T F1 = rc1_minus1_over_e(ee, fail);
-                T dx1 = cst<T>(2.0) * s1 * pprod(padd(sp, s1));
-                T ddp = f * (pprod(padd(sp, sq)) + cst<T>(2.0) * s1 * (sq + s1 + psum(sp))) / (sq + s1);
-                sDD = sDD + f * (eh * F1 / d - ddp / (d * dx1));
-            }
-        }
-        x1 = (x1 + lam) * cst<T>(0.25);
-        // pair members: y_a + lam = (s_a + s1)(s_a + s_b) with s = sqrt(y), a
-        // product of sums of numbers with non-negative real parts, so no
-        // cancellation when y lies near the negative real axis (there
-        // y + |s|^2 = s (s + conj s) is small: near the no-Big-Bang boundary)
-        pr = pscale(padd(sp, s1), psum(sp) * cst<T>(0.25));
-#pragma unroll
-        for (int j = 0; j < NJ; j++) p[j] = (p[j] + lam) * cst<T>(0.25);
-        f = f * cst<T>(0.25);
-    }
-    if (m == Prec<T>::maxit) *fail = 1;
-    // R_F series
-    {
-        T A = (x1 + psum(pr)) * cst<T>(1.0 / 3.0), iA = cst<T>(1.0) / A;
-        T X = (A - x1) * iA;
-        PT Y = pscale(prsub(A, pr), iA);
-        T e2 = X * psum(Y) + pprod(Y), e3 = X * pprod(Y);
-        T ser = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
-                - e2 * e3 * cst<T>(3.0 / 44.0);
-        R.RF = ser / ssqrt(A) * h;
-    }
-    if (WANT_D) {
-        T A = (psum(pr) + cst<T>(3.0) * x1) * cst<T>(0.2), iA = cst<T>(1.0) / A;
-        T X = (A - x1) * iA;
-        PT Y = pscale(prsub(A, pr), iA);
-        T ser = rj_series<T, T>(X, psum(Y), pprod(Y), X);
-        R.RD1 = (f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1) * g * h;
-    }
-    if (WANT_DP) R.RDp = pscale(pscale(rd_pair_series(x1, pr, f, sDp), g), h);
-    else R.RDp = pzero(pr);
-#pragma unroll
-    for (int j = 0; j < (DDL ? NJ - 1 : NJ); j++) {
-        T A = (x1 + psum(pr) + cst<T>(2.0) * p[j]) * cst<T>(0.2), iA = cst<T>(1.0) / A;
-        T X = (A - x1) * iA, P = (A - p[j]) * iA;
-        PT Y = pscale(prsub(A, pr), iA);
-        T ser = rj_series<T, T>(X, psum(Y), pprod(Y), P);
-        R.RJ[j] = (f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j]) * g * h;
-    }
-    if (DDL) {
-        // final series: A(u) = (sig + 2u)/5 at u1 = p, u2 = x1; X = 1 - x1/A,
-        // Y = 1 - pair/A, P = 1 - u/A; divided differences by the product rule
-        const T sig = x1 + psum(pr);
-        const T u1 = x1 + hs * f;   // p after m steps (p - x1 shrinks by 4 each step)
-        T A1 = (sig + cst<T>(2.0) * u1) * cst<T>(0.2), A2 = (sig + cst<T>(2.0) * x1) * cst<T>(0.2);
-        T iA1 = cst<T>(1.0) / A1, iA2 = cst<T>(1.0) / A2;
-        T dInv = cst<T>(-0.4) * iA1 * iA2;                 // [1/A]
-        DD<T> inv = mkdd<T>(iA1, iA2, dInv);
-        DD<T> X = cst<T>(1.0) - inv * x1;
-        DD<T> sY = cst<T>(2.0) - inv * psum(pr);
-        DD<T> inv2 = inv * inv;
-        DD<T> pY = (cst<T>(1.0) - inv * psum(pr)) + inv2 * pprod(pr);
-        DD<T> P = mkdd<T>(cst<T>(1.0) - u1 * iA1, cst<T>(1.0) - x1 * iA2, sig * cst<T>(-0.2) * iA1 * iA2);
-        DD<T> ser = rj_series<DD<T>, T>(X, sY, pY, P);
-        // [A^-3/2] = -(2/5)(A1 + sqrt(A1 A2) + A2) / ((sqrt A1 + sqrt A2) A1^3/2 A2^3/2)
-        T r1 = ssqrt(A1), r2 = ssqrt(A2);
-        T a32_1 = iA1 / r1, a32_2 = iA2 / r2;
-        T dA32 = cst<T>(-0.4) * (A1 + r1 * r2 + A2) / (r1 + r2) * a32_1 * a32_2;
-        T dser = dA32 * ser.v1 + a32_2 * ser.d;          // [A^-3/2 S]
-        // R_J(p) - R_D = f (T(u1) - T(u2)) + 6 (sum_p - sum_x1), T = A^-3/2 S,
-        // with u1 - u2 = f hs and the sums' difference = hs sDD
-        R.DJ = (f * f * dser + cst<T>(6.0) * sDD) * g * g * h;
-        // R_J(x1 + hl) = R_D(x2, x3, x1) + hl DJ: a sum, no cancellation
-        R.RJ[NJ - 1] = R.RD1 + hl * R.DJ;
-    }
-    return R;
 }
 
 // ---------------------------------------------------------------------------
@@ -738,7 +514,10 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
             T ee = f3 * delta[j] / (d * d);
             if (!(DDL && j == NJ - 1)) sJ[j] = sJ[j] + f * rc1(ee, fail) / d;
             if (DDL && j == NJ - 1) {
-                // as in carlson_dup, with g(b) = x1 + lambda and g(a) = g
+                // [R_C(1,1+e)/d_p - 1/d_x1] / h with e/h = f^3 Pi / d_p^2 and
+                // (d_p - d_x1)/h = f [g(a) + 2b (a + b + S)] / (a + b),
+                // a = sqrt(p), b = s1, g(v) = (v + s_a)(v + s_b), d_x1 = 2 b g(b),
+                // g(b) = x1 + lambda
                 T eh = f3 * PiL / (d * d);
                 T F1 = rc1_minus1_over_e(ee, fail);
                 T dx1 = cst<T>(2.0) * s1 * xl;
@@ -783,7 +562,10 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
     }
     R.DJ = R.RD1;
     if (DDL) {
-        // the final series' divided difference, as in carlson_dup
+        // final series: A(u) = (sig + 2u)/5 at u1 = p, u2 = x1; X = 1 - x1/A,
+        // Y = 1 - pair/A, P = 1 - u/A; divided differences by the product rule,
+        // [A^-3/2] = -(2/5)(A1 + sqrt(A1 A2) + A2) / ((sqrt A1 + sqrt A2) A1^3/2 A2^3/2);
+        // R_J(p) - R_D = f (T(u1) - T(u2)) + 6 (sum_p - sum_x1), T = A^-3/2 S
         const T sgm = x1 + sig;
         const T u1 = x1 + hs * f;
         T A1 = (sgm + cst<T>(2.0) * u1) * cst<T>(0.2), A2 = (sgm + cst<T>(2.0) * x1) * cst<T>(0.2);
