@@ -153,6 +153,24 @@ template <class T, int K> LCDM_HD Dual<T, K> ssqrt(const Dual<T, K>& a) {
     for (int k = 0; k < K; k++) r.d[k] = a.d[k] * h;
     return r;
 }
+// FP32: one reciprocal square root gives both the value (a rsqrt(a)) and the
+// tangents' factor (rsqrt(a)/2), one special-function operation instead of two
+LCDM_HD float srsqrt(float a) {
+#ifdef __CUDA_ARCH__
+    return rsqrtf(a);
+#else
+    return 1.0f / sqrtf(a);
+#endif
+}
+template <int K> LCDM_HD Dual<float, K> ssqrt(const Dual<float, K>& a) {
+    Dual<float, K> r;
+    const float rs = srsqrt(a.v);
+    r.v = a.v > 0.f ? a.v * rs : sqrtf(a.v);
+    const float h = 0.5f * rs;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = a.d[k] * h;
+    return r;
+}
 template <class T, int K> LCDM_HD Dual<T, K> sabs(const Dual<T, K>& a) { return sval(a.v) < 0 ? -a : a; }
 // value with a given gradient: r = v + sum_k g_k * (tangent_k of the inputs), built by callers
 template <class T, int K> LCDM_HD Dual<T, K> dlin(T v, T g, const Dual<T, K>& x) {
@@ -333,6 +351,26 @@ template <class T> LCDM_HD T rc1(T e, int* fail) {
     return rc_value(cst<T>(1.0), cst<T>(1.0) + e, fail);
 }
 
+// With tangents: the series and its derivative by one Horner pass in plain
+// arithmetic, applied to e's tangents once (d R_C(1, 1+e)/de = -s'(w), w = -e).
+template <class T, int K> LCDM_HD Dual<T, K> rc1(const Dual<T, K>& e, int* fail) {
+    if (sval(sabs(e.v)) <= sval(Prec<T>::rc_series_max())) {
+        const T w = -e.v;
+        T s = cst<T>(1.0 / (2 * Prec<T>::rc_terms + 1)), ds = cst<T>(0.0);
+#pragma unroll
+        for (int n = Prec<T>::rc_terms - 1; n >= 0; n--) {
+            ds = ds * w + s;
+            s = cst<T>(1.0 / (2 * n + 1)) + w * s;
+        }
+        Dual<T, K> r;
+        r.v = s;
+#pragma unroll
+        for (int k = 0; k < K; k++) r.d[k] = -ds * e.d[k];
+        return r;
+    }
+    return rc_value(dconst<T, K>(cst<T>(1.0)), dconst<T, K>(cst<T>(1.0)) + e, fail);
+}
+
 // (R_C(1, 1+e) - 1) / e = sum_{n>=1} (-e)^n / (2n+1) / e, without cancellation.
 template <class T> LCDM_HD T rc1_minus1_over_e(T e, int* fail) {
     if (sval(sabs(e)) <= sval(Prec<T>::rc_series_max())) {
@@ -357,6 +395,63 @@ template <class U, class T> LCDM_HD U rj_series(U X, U sumY, U prodY, U P) {
     U E5 = XYZ * P2;
     return cst<T>(1.0) - E2 * cst<T>(3.0 / 14.0) + E3 * cst<T>(1.0 / 6.0) + E2 * E2 * cst<T>(9.0 / 88.0)
            - E4 * cst<T>(3.0 / 22.0) - E2 * E3 * cst<T>(9.0 / 52.0) + E5 * cst<T>(3.0 / 26.0);
+}
+
+// The R_F and R_J series of the duplication's last step, as plain numbers or
+// with tangents.  For dual numbers the series' partial derivatives with
+// respect to its four inputs are formed by hand (reverse mode through the
+// polynomial, in plain arithmetic) and applied to the inputs' tangents once:
+// a fraction of the cost of carrying K tangents through every product.
+//   R_F: 1 - e2/10 + e3/14 + e2^2/24 - 3 e2 e3/44,  e2 = X sY + pY, e3 = X pY.
+template <class S> LCDM_HD S rf_ser(const S& X, const S& sY, const S& pY) {
+    typedef typename Base<S>::type T;
+    S e2 = X * sY + pY, e3 = X * pY;
+    return cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
+           - e2 * e3 * cst<T>(3.0 / 44.0);
+}
+template <class T, int K> LCDM_HD Dual<T, K> rf_ser(const Dual<T, K>& X, const Dual<T, K>& sY, const Dual<T, K>& pY) {
+    const T x = X.v, sy = sY.v, py = pY.v;
+    const T e2 = x * sy + py, e3 = x * py;
+    Dual<T, K> r;
+    r.v = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
+          - e2 * e3 * cst<T>(3.0 / 44.0);
+    const T g2 = cst<T>(-0.1) + e2 * cst<T>(1.0 / 12.0) - e3 * cst<T>(3.0 / 44.0);
+    const T g3 = cst<T>(1.0 / 14.0) - e2 * cst<T>(3.0 / 44.0);
+    const T gx = g2 * sy + g3 * py, gs = g2 * x, gp = g2 + g3 * x;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = gx * X.d[k] + gs * sY.d[k] + gp * pY.d[k];
+    return r;
+}
+//   R_J (rj_series above): Q = X pY, E2 = X sY + pY - 3P^2, E3 = Q + 2 E2 P + 4 P^3,
+//   E4 = (2Q + E2 P + 3P^3) P, E5 = Q P^2.
+template <class S> LCDM_HD S rj_ser(const S& X, const S& sY, const S& pY, const S& P) {
+    return rj_series<S, typename Base<S>::type>(X, sY, pY, P);
+}
+template <class T, int K>
+LCDM_HD Dual<T, K> rj_ser(const Dual<T, K>& X, const Dual<T, K>& sY, const Dual<T, K>& pY, const Dual<T, K>& P) {
+    const T x = X.v, sy = sY.v, py = pY.v, p = P.v;
+    const T Q = x * py, P2 = p * p, P3 = P2 * p;
+    const T E2 = x * sy + py - P2 * cst<T>(3.0);
+    const T E3 = Q + E2 * p * cst<T>(2.0) + P3 * cst<T>(4.0);
+    const T W = Q * cst<T>(2.0) + E2 * p + P3 * cst<T>(3.0);
+    const T E4 = W * p, E5 = Q * P2;
+    Dual<T, K> r;
+    r.v = cst<T>(1.0) - E2 * cst<T>(3.0 / 14.0) + E3 * cst<T>(1.0 / 6.0) + E2 * E2 * cst<T>(9.0 / 88.0)
+          - E4 * cst<T>(3.0 / 22.0) - E2 * E3 * cst<T>(9.0 / 52.0) + E5 * cst<T>(3.0 / 26.0);
+    // adjoints of the intermediates (d series / d E_i), then back to the inputs
+    const T gE3 = cst<T>(1.0 / 6.0) - E2 * cst<T>(9.0 / 52.0);
+    const T gE4 = cst<T>(-3.0 / 22.0), gE5 = cst<T>(3.0 / 26.0);
+    const T gW = gE4 * p;
+    const T gE2 = cst<T>(-3.0 / 14.0) + E2 * cst<T>(9.0 / 44.0) - E3 * cst<T>(9.0 / 52.0) + gW * p
+                  + gE3 * p * cst<T>(2.0);
+    const T gQ = gE5 * P2 + gW * cst<T>(2.0) + gE3;
+    const T gP3 = gW * cst<T>(3.0) + gE3 * cst<T>(4.0);
+    const T gP2 = gE5 * Q - gE2 * cst<T>(3.0) + gP3 * p;
+    const T gp = gE4 * W + gW * E2 + gE3 * E2 * cst<T>(2.0) + gP3 * P2 + gP2 * p * cst<T>(2.0);
+    const T gx = gE2 * sy + gQ * py, gs = gE2 * x, gy = gE2 + gQ * x;
+#pragma unroll
+    for (int k = 0; k < K; k++) r.d[k] = gx * X.d[k] + gs * sY.d[k] + gy * pY.d[k] + gp * P.d[k];
+    return r;
 }
 
 // Divided-difference numbers: the values of a quantity at two points u1, u2
@@ -538,16 +633,14 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
         T A = (x1 + sig) * cst<T>(1.0 / 3.0), iA = cst<T>(1.0) / A;
         T X = (A - x1) * iA;
         T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
-        T e2 = X * sY + pY, e3 = X * pY;
-        T ser = cst<T>(1.0) - e2 * cst<T>(0.1) + e3 * cst<T>(1.0 / 14.0) + e2 * e2 * cst<T>(1.0 / 24.0)
-                - e2 * e3 * cst<T>(3.0 / 44.0);
+        T ser = rf_ser(X, sY, pY);
         R.RF = ser / ssqrt(A) * h;
     }
     if (WANT_D) {
         T A = (sig + cst<T>(3.0) * x1) * cst<T>(0.2), iA = cst<T>(1.0) / A;
         T X = (A - x1) * iA;
         T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
-        T ser = rj_series<T, T>(X, sY, pY, X);
+        T ser = rj_ser(X, sY, pY, X);
         R.RD1 = (f * ser * iA / ssqrt(A) + cst<T>(3.0) * sD1) * g * h;
     } else {
         R.RD1 = R.RF;
@@ -557,7 +650,7 @@ LCDM_HD SymResult<T, NJ> carlson_sym(T s1, T S, T P, bool cplx, const T* pj, con
         T A = (x1 + sig + cst<T>(2.0) * p[j]) * cst<T>(0.2), iA = cst<T>(1.0) / A;
         T X = (A - x1) * iA, Pp = (A - p[j]) * iA;
         T sY = (A + A - sig) * iA, pY = ((A - sig) * A + pi) * (iA * iA);
-        T ser = rj_series<T, T>(X, sY, pY, Pp);
+        T ser = rj_ser(X, sY, pY, Pp);
         R.RJ[j] = (f * ser * iA / ssqrt(A) + cst<T>(6.0) * sJ[j]) * g * h;
     }
     R.DJ = R.RD1;
