@@ -272,6 +272,12 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
         int settled = 0;
         double prev = 1e300;
         bool done = !active;
+        // Isolated roots (every one more than a tenth of its modulus from the
+        // others, judged on the single-precision approximations): the
+        // iteration converges cubically from ~1e-6, so one FP64 sweep whose
+        // corrections are all below 1e-6 leaves them within rounding and no
+        // confirming sweep is needed.
+        bool iso = true;
 #pragma unroll 1
         for (int it = 0; it < 200; it++) {
             double br[4], bi[4];
@@ -279,6 +285,18 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
             for (int k = 0; k < 4; k++) {
                 br[k] = G == 1 ? zre[k / G] : __shfl_sync(full, zre[k / G], k % G, G);
                 bi[k] = G == 1 ? zim[k / G] : __shfl_sync(full, zim[k / G], k % G, G);
+            }
+            if (it == 0) {
+#pragma unroll 1
+                for (int j = 0; j < n; j++) {
+                    const float mj = sqrtf((float)(br[j] * br[j] + bi[j] * bi[j]));
+#pragma unroll 1
+                    for (int k = 0; k < n; k++) {
+                        if (k == j) continue;
+                        const float dr_ = (float)(br[j] - br[k]), di_ = (float)(bi[j] - bi[k]);
+                        if (!(sqrtf(dr_ * dr_ + di_ * di_) > 0.1f * mj)) iso = false;
+                    }
+                }
             }
             double worst = 0.0;
 #pragma unroll
@@ -307,7 +325,7 @@ template <int G> __device__ void group_roots(const double* c, const double* alph
                 }
             }
             if (!done) {
-                if (worst < 1e-30) { if (++settled >= 1) done = true; }
+                if (worst < 1e-30 || (it == 0 && iso && worst < 1e-12)) { if (++settled >= 1) done = true; }
                 else if (it >= 4 && worst >= 0.25 * prev && worst < 1e-24) done = true;
                 prev = worst;
             }
