@@ -365,7 +365,7 @@ def main():
     off_h = offsets.cpu().contiguous()
     z_h = z.cpu().pin_memory()
     cot_h = {n: v.cpu().pin_memory() for n, v in cot.items()}
-    host = lcdm.HostVJP(B, npairs, outputs=OUTPUTS, precision="fp32", nchunks=12, device=dev,
+    host = lcdm.HostVJP(B, npairs, outputs=OUTPUTS, precision="fp32", nchunks=5, device=dev,
                         block=(tune or {}).get("block", 0), blocks_per_sm=(tune or {}).get("blocks_per_sm", 0),
                         lane_map=(tune or {}).get("lane_map", "tuned"))
     h2d = p_h.numel() * 8 + off_h.numel() * 8 + z_h.numel() * 4 + sum(v.numel() * 4 for v in cot_h.values())
@@ -437,7 +437,7 @@ def main():
                     "launch": tune, "wall_s_timed": t_wall}),
                 "gpu_launches": launches, "clocks": clocks, "roofline": roof,
                 "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                        "ms_per_step": e2e_ms, "api": "lcdm_distances_vjp_host, 12 chunks, page-locked host arrays"},
+                        "ms_per_step": e2e_ms, "api": "lcdm_distances_vjp_host, 5 chunks (ramped 1 2 3 2 1), page-locked host arrays"},
                 "cpu_baseline": cpu}
         line.update(extra)
         if not args.no_vi:

@@ -231,10 +231,11 @@ lcdm_status lcdm_host_workspace_size(int64_t B, int64_t n, const lcdm_opts* opts
  * offsets [B+1], z [n], cot[o] [n], out[o] [n] (out and each entry may be
  * NULL), grad [B][ncol] and cosmo_status [B] are all host arrays; CSR layout
  * only.  The paper's method is unchanged (Sec. 3); this entry point only moves
- * the data.  The batch is cut into nchunks (1..64) runs of whole rows with
- * about n / nchunks pairs each; the host-to-device copies of the next run and
- * the device-to-host copies of the previous one overlap the pair kernel of the
- * current run.  The copies run on two streams that the library creates once
+ * the data.  The batch is cut into nchunks (1..64) runs of whole rows whose
+ * pair counts ramp up and down in the proportions 1 2 3 ... 3 2 1 (small
+ * first and last runs: their copies are not overlapped); the host-to-device
+ * copies of the next run and the device-to-host copies of the previous one
+ * overlap the pair kernels of the current run.  The copies run on two streams that the library creates once
  * per device (first call); the kernels run on `stream`, after the work already
  * queued there.  Page-locked host arrays are needed for the copies to overlap.
  *   dws: device workspace of lcdm_host_workspace_size(B, n, opts) bytes,

@@ -246,6 +246,25 @@ lcdm_status launch_plan(Plan& P, int block, int bps, int lane_map, cudaStream_t 
     return launch_one(P, block, bps, lane_map, s);
 }
 
+// Resident blocks per SM of a pair kernel, queried once per (device, kernel,
+// block size): the query is host work on every launch otherwise (the chunked
+// host entry point launches twice per chunk).
+int cached_occ(const PairsTable& t, int idx, int prec, int K, int block) {
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, int, int, int>, int> cache;
+    const auto key = std::make_tuple(current_device(), prec, K, idx, block);
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) return it->second;
+    }
+    const int occ = t.occ[idx](block);
+    if (occ > 0) {
+        std::lock_guard<std::mutex> lk(mu);
+        cache[key] = occ;
+    }
+    return occ;
+}
 lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s) {
     const PairsTable& t = table(P.prec, P.K);
     int idx = (P.wt ? 2 : 0) + (P.wx ? 1 : 0);
@@ -260,7 +279,7 @@ lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s
     }
     P.args.interleave = lane_map == LCDM_MAP_INTERLEAVED ? 1 : 0;
     if (block == 0) block = 256;   // one full-SM block per SM, warps in lockstep (see pairs_kernel)
-    int occ = t.occ[idx](block);
+    int occ = cached_occ(t, idx, P.prec, P.K, block);
     if (occ <= 0) return LCDM_ERR_CUDA;
     if (bps == 0 || bps > occ) bps = occ;
     int64_t warps = (int64_t)num_sms() * bps * (block / 32);
@@ -766,11 +785,22 @@ lcdm_status lcdm_distances_vjp_host(const double* params, int64_t B, const int64
     if (!ok) return LCDM_ERR_CUDA;
     st = run_prep(d.params, B, opts, d.rec, d.status, d.grad, nullptr, stream);
     if (st != LCDM_OK) return st;
-    // chunk c covers rows [rb[c], rb[c+1]) with about n / nchunks pairs each
+    // chunk c covers rows [rb[c], rb[c+1]); its share of the pairs ramps up and
+    // down, weights min(c + 1, nchunks - c, 3) (1 2 3 ... 3 2 1): the first
+    // chunk's input copy and the last chunk's output copy are the parts of the
+    // pipeline that nothing overlaps, and each step of the ramp at most doubles
+    // (or halves) a chunk, so the next chunk's copy still hides behind the
+    // current chunk's kernels
     int64_t rb[LCDM_HOST_MAX_CHUNKS + 1];
+    int64_t wcum[LCDM_HOST_MAX_CHUNKS + 1];
+    wcum[0] = 0;
+    for (int c = 0; c < nchunks; c++) {
+        int w = c + 1 < nchunks - c ? c + 1 : nchunks - c;
+        wcum[c + 1] = wcum[c] + (w < 3 ? w : 3);
+    }
     rb[0] = 0;
     for (int c = 1; c < nchunks; c++) {
-        const int64_t target = n * c / nchunks;
+        const int64_t target = (int64_t)((double)n * (double)wcum[c] / (double)wcum[nchunks]);
         int64_t lo = rb[c - 1], hi = B;   // first row whose start offset is >= target
         while (lo < hi) {
             int64_t mid = (lo + hi) / 2;
