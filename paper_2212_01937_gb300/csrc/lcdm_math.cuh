@@ -70,7 +70,14 @@ LCDM_HD df64 operator+(df64 a, df64 b) {
     s.lo = LCDM_FADD(s.lo, t.lo);
     return fast_two_sum(s.hi, s.lo);
 }
-LCDM_HD df64 operator+(df64 a, float b) { return a + mkdf(b); }
+// a + b for a plain float b: one error-free sum of the high words, the low
+// word and the rounding error added, renormalised (about half the work of the
+// double-float sum)
+LCDM_HD df64 operator+(df64 a, float b) {
+    df64 s = two_sum(a.hi, b);
+    s.lo = LCDM_FADD(s.lo, a.lo);
+    return fast_two_sum(s.hi, s.lo);
+}
 
 // ---------------------------------------------------------------------------
 // Scalar traits: value used for branching, sqrt, abs, constants.
