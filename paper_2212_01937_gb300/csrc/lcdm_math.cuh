@@ -245,6 +245,23 @@ template <class S> LCDM_HD Cx<S> cxsqrt(const Cx<S>& a) {
     return mkcx<S>(ai / (t + t), neg_im ? -t : t);
 }
 
+// With tangents: the value by the plain complex square root, the tangents as
+// d sqrt(a) = da / (2 sqrt(a)) with one complex reciprocal for all of them.
+template <class T, int K> LCDM_HD Cx<Dual<T, K> > cxsqrt(const Cx<Dual<T, K> >& a) {
+    const Cx<T> sv = cxsqrt(mkcx<T>(a.re.v, a.im.v));
+    const T h = cst<T>(0.5) / (sv.re * sv.re + sv.im * sv.im);
+    const T cr = sv.re * h, ci = -(sv.im * h);      // 1 / (2 sqrt(a))
+    Cx<Dual<T, K> > r;
+    r.re.v = sv.re;
+    r.im.v = sv.im;
+#pragma unroll
+    for (int k = 0; k < K; k++) {
+        r.re.d[k] = a.re.d[k] * cr - a.im.d[k] * ci;
+        r.im.d[k] = a.re.d[k] * ci + a.im.d[k] * cr;
+    }
+    return r;
+}
+
 // ---------------------------------------------------------------------------
 // Root / argument pairs.  A pair is two numbers that are either complex
 // conjugates (CPair, stores the first member) or two reals (RPair).
