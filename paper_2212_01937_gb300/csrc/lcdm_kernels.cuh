@@ -418,11 +418,13 @@ __global__ void __launch_bounds__(256, MinBlocks<PREC, K, WX>::value) pairs_kern
     }
     const int64_t len = end - start, nb = (len + 31) / 32, nb_all = a.chunk / 32;
     const int64_t s_lane = a.interleave ? nb : 1, s_it = a.interleave ? 1 : 32;
-    // With a full-SM block (256 threads, one block per SM) the warps step through
-    // their ranges together, one 32-pair batch at a time: the fused code of a pair
-    // is about the size of the instruction cache, and warps at the same place in
-    // it share each fetched line.  Every warp runs nb_all steps (the same number).
-    const bool lockstep = blockDim.x == 256;
+    // With a full-SM block (256 threads) the warps of the kernels whose code per
+    // pair is largest (X's tangents, seven-column tangents) step through their
+    // ranges together, one 32-pair batch at a time: that code is about the size
+    // of the instruction cache, and warps at the same place in it share each
+    // fetched line.  Every warp then runs nb_all steps (the same number).  For
+    // the other kernels the barrier costs more than it saves (measured).
+    const bool lockstep = blockDim.x == 256 && K > 0 && (WX || K > 3);
     for (int64_t it = 0; it < nb_all; it++) {
         if (lockstep) __syncthreads();
         if (it >= nb) continue;
@@ -448,6 +450,15 @@ __global__ void __launch_bounds__(256, MinBlocks<PREC, K, WX>::value) pairs_kern
         const float2* rf = a.recF + row * NREC;
         const int st = a.status[row];
         const TO z = load_io<TO>(a.z, zi);
+        // the pair's cotangents (or observed magnitude) are loaded before the
+        // evaluation, so that their latency hides behind it
+        TO gcot[N_OUT];
+        TO mob = (TO)0;
+        if constexpr (K > 0) {
+#pragma unroll
+            for (int i = 0; i < N_OUT; i++) gcot[i] = (reduce && !loglike && a.cot[i]) ? load_io<TO>(a.cot[i], pidx) : (TO)0;
+            if (loglike) mob = load_io<TO>(a.mobs, zi);
+        }
         PairOut<TO, K> o;
         int fail = 0;
         if (st == ST_OK) {
@@ -482,7 +493,7 @@ __global__ void __launch_bounds__(256, MinBlocks<PREC, K, WX>::value) pairs_kern
         for (int i = 0; i < NV; i++) c[i] = 0;
         if (active && st == ST_OK && !fail) {
             if (loglike) {
-                TO r = (load_io<TO>(a.mobs, zi) - o.v[O_MU] - Mobs) * inv_sig;
+                TO r = ((K > 0 ? mob : load_io<TO>(a.mobs, zi)) - o.v[O_MU] - Mobs) * inv_sig;
                 TO w = r * inv_sig;
                 c[0] = w * o.h0[O_MU];
 #pragma unroll
@@ -492,7 +503,7 @@ __global__ void __launch_bounds__(256, MinBlocks<PREC, K, WX>::value) pairs_kern
 #pragma unroll
                 for (int i = 0; i < N_OUT; i++) {
                     if (!a.cot[i]) continue;
-                    TO g = load_io<TO>(a.cot[i], pidx);
+                    TO g = K > 0 ? gcot[i] : load_io<TO>(a.cot[i], pidx);
                     c[0] += g * o.h0[i];
 #pragma unroll
                     for (int k = 0; k < K; k++) c[1 + k] += g * o.d[i][k];
