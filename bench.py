@@ -44,8 +44,8 @@ ALG_MUFU_PER_PAIR = 390.3
 # tangent launch) and their DRAM bytes (read + write) per step, from one ncu
 # capture of both launches on this workload (profiles/pairs_kernel_fp32_vjp_
 # 4096x1024.md; to be set to None whenever the kernels change until re-taken).
-EXEC_FLOP_PER_PAIR = None
-TRAFFIC_BYTES = None
+EXEC_FLOP_PER_PAIR = 2340.6
+TRAFFIC_BYTES = 110.1e6
 # Derived peaks (unit counts x maximum SM clock): FP32 FMA, 152 SMs x 128 lanes
 # x 2 flops; special-function unit, 152 SMs x 16 per clock.
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
