@@ -278,7 +278,7 @@ lcdm_status launch_one(Plan& P, int block, int bps, int lane_map, cudaStream_t s
         }
     }
     P.args.interleave = lane_map == LCDM_MAP_INTERLEAVED ? 1 : 0;
-    if (block == 0) block = 256;   // one full-SM block per SM, warps in lockstep (see pairs_kernel)
+    if (block == 0) block = 256;   // full-size blocks (the largest kernels step in lockstep, see pairs_kernel)
     int occ = cached_occ(t, idx, P.prec, P.K, block);
     if (occ <= 0) return LCDM_ERR_CUDA;
     if (bps == 0 || bps > occ) bps = occ;
