@@ -5,8 +5,9 @@
 // Carlson integrals enter through carlson_any / rc_any.  Their tangents are
 // carried through one shared duplication sequence as dual numbers (see
 // carlson_any); R_C's tangents use dR_F/dx_m = -R_D(..x_m..)/6 (eq. 2.10) with
-// R_C(x, y) = R_F(x, y, y).  All R_D, R_J and R_F values come from one shared
-// duplication sequence.
+// R_C(x, y) = R_F(x, y, y) and Euler's relation for the R_D that has a pair
+// member special (rc_value_grad).  All R_D, R_J and R_F values of a pair come
+// from one shared duplication sequence.
 //
 // Cauchy principal values (Sec. 2.2) for negative p or y:
 //   (q+z) R_J(x,y,z,-q) = (s-z) R_J(x,y,z,s) - 3 R_F + 3 sqrt(xyz/(xy+sq)) R_C(xy+sq, sq),
@@ -123,7 +124,8 @@ template <class T, int K> LCDM_HD Dual<T, K> rc_any(const Dual<T, K>& x, const D
 // oracle, the formulas left d t / d theta at 2e-2 for Omega_L0 = 1e-12 (a
 // near-double root at rho = 0) and d X / d Omega_r0 at 3e-5 for
 // Omega_r0 = 1e-12, where the dual tangents give 5e-14 and 4e-13.  Only
-// R_C's tangents use (2.10) (R_C(x, y) = R_F(x, y, y), no differences).
+// R_C's tangents use (2.10) (R_C(x, y) = R_F(x, y, y), no differences; see
+// rc_value_grad).
 // Phi(w) = [R_C(1, 1-w) - (1-w)^-1/2] / w: the part of R_C(y + d, y) - y^-1/2
 // that is linear in w = d / (y + d), as a series for small w (coefficients
 // 1/(2n+1) - C(2n,n)/4^n, n >= 1) and directly otherwise.
